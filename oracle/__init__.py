@@ -1,0 +1,198 @@
+"""FP64 CPU oracle of the spatio-spectral ADMM (arXiv:1504.06847, Algorithm 1).
+
+TEST INFRASTRUCTURE.  Only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package.  It shares no code with
+the CUDA library: its FFT, wavelet transform, DCT and filters are its own
+(``mf_oracle.c`` and ``daubechies.py``).
+
+Python-side helpers here only marshal numpy arrays into the C library, which
+holds the arithmetic of every step.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+from . import daubechies
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mf_oracle.c")
+_LIB = os.path.join(_HERE, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+MAXF = 16
+NHIST = 8
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP64, -O2, no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off",
+                               "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int)
+            c_int = ctypes.c_int
+            L.orc_fft2.argtypes = [dp, dp, c_int, c_int, c_int]
+            L.orc_dwt2.argtypes = [dp, dp, c_int, c_int, c_int, dp, c_int, c_int]
+            L.orc_dct_matrix.argtypes = [c_int, dp]
+            L.orc_setup.argtypes = [c_int, c_int, dp, dp, dp, dp, dp, dp, dp]
+            L.orc_setup.restype = c_int
+            L.orc_solve.argtypes = [c_int, c_int, c_int, c_int, ip, dp, dp, dp, dp, dp, dp]
+            L.orc_solve.restype = c_int
+            L.orc_make_b.argtypes = [c_int, c_int, c_int, c_int, ip, dp, dp] + [dp] * 8
+            L.orc_make_b.restype = c_int
+            L.orc_primal_dual.argtypes = [c_int, c_int, c_int, c_int, ip, dp, dp] + [dp] * 9
+            L.orc_primal_dual.restype = c_int
+            L.orc_iterate.argtypes = ([c_int, c_int, c_int, c_int, ip, dp, dp] + [dp] * 5 +
+                                      [dp] * 9 + [c_int, dp])
+            L.orc_iterate.restype = c_int
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    assert a.dtype == np.int32 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+# ---------------------------------------------------------------------------
+# Transforms (exposed for the pins)
+# ---------------------------------------------------------------------------
+
+def fft2(x: np.ndarray, inverse: bool = False) -> np.ndarray:
+    """Unnormalised 2-D DFT of each N x N image of x (complex128 [..., N, N])."""
+    x = np.asarray(x, dtype=np.complex128)
+    N = x.shape[-1]
+    re = np.ascontiguousarray(x.real.reshape(-1, N, N))
+    im = np.ascontiguousarray(x.imag.reshape(-1, N, N))
+    lib().orc_fft2(_p(re), _p(im), N, re.shape[0], 1 if inverse else -1)
+    return (re + 1j * im).reshape(x.shape)
+
+
+def dwt2(x: np.ndarray, h: np.ndarray, J: int, inverse: bool = False) -> np.ndarray:
+    """J-level periodic 2-D wavelet analysis (or synthesis) of each image."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    N = x.shape[-1]
+    src = x.reshape(-1, N, N)
+    out = np.empty_like(src)
+    hh = np.zeros(MAXF)
+    hh[: len(h)] = h
+    lib().orc_dwt2(_p(src), _p(out), N, src.shape[0], J, _p(hh), len(h), -1 if inverse else 1)
+    return out.reshape(x.shape)
+
+
+def dct_matrix(L: int) -> np.ndarray:
+    C = np.empty((L, L))
+    lib().orc_dct_matrix(L, _p(C))
+    return C
+
+
+# ---------------------------------------------------------------------------
+# Problem and state
+# ---------------------------------------------------------------------------
+
+PARAM_ORDER = ("mu_eps", "mu_s", "mu_nu", "rho_P", "rho_T", "rho_V", "rho_S")
+
+
+class Problem:
+    """A cube (psf, y) with its regularisation, dictionary and level count."""
+
+    def __init__(self, psf, y, params: dict, J: int = 3, mask: int = 0x1FF, bases=None):
+        self.psf = np.ascontiguousarray(psf, dtype=np.float64)
+        self.y = np.ascontiguousarray(y, dtype=np.float64)
+        self.L, self.N = self.y.shape[0], self.y.shape[-1]
+        assert self.psf.shape == self.y.shape == (self.L, self.N, self.N)
+        self.J = J
+        self.bases = bases if bases is not None else daubechies.dictionary(mask)
+        self.nb = len(self.bases)
+        self.F = np.array([len(h) for _, h in self.bases], dtype=np.int32)
+        self.h = np.zeros((self.nb, MAXF))
+        for k, (_, h) in enumerate(self.bases):
+            self.h[k, : len(h)] = h
+        self.params = dict(params)
+        self.prm = np.array([float(self.params[k]) for k in PARAM_ORDER])
+        shp = (self.L, self.N, self.N)
+        self.hre, self.him = np.empty(shp), np.empty(shp)
+        self.yre, self.yim = np.empty(shp), np.empty(shp)
+        self.HtY = np.empty(shp)
+        rc = lib().orc_setup(self.N, self.L, _p(self.psf), _p(self.y), _p(self.hre), _p(self.him),
+                             _p(self.yre), _p(self.yim), _p(self.HtY))
+        assert rc == 0
+
+    @property
+    def rho_bar(self):
+        p = self.params
+        return p["mu_eps"] + p["rho_S"] + p["rho_P"] + self.nb * p["rho_T"]
+
+    def _hdr(self):
+        return (self.N, self.L, self.J, self.nb, _ip(self.F), _p(self.h), _p(self.prm))
+
+    def zero_state(self) -> dict:
+        shp = (self.L, self.N, self.N)
+        st = {k: np.zeros(shp) for k in ("X", "P", "V", "S", "GP", "GV", "GS")}
+        st["T"] = np.zeros((self.nb,) + shp)
+        st["GT"] = np.zeros((self.nb,) + shp)
+        return st
+
+    def iterate(self, state: dict, n_iter: int, hist: bool = False):
+        """Run Algorithm 1 for n_iter iterations, updating `state` in place.
+        Returns the per-iteration history array [n_iter, NHIST] (or None)."""
+        H = np.zeros((n_iter, NHIST)) if hist else None
+        s = state
+        rc = lib().orc_iterate(*self._hdr(), _p(self.hre), _p(self.him), _p(self.yre),
+                               _p(self.yim), _p(self.HtY), _p(s["X"]), _p(s["P"]), _p(s["T"]),
+                               _p(s["V"]), _p(s["S"]), _p(s["GP"]), _p(s["GT"]), _p(s["GV"]),
+                               _p(s["GS"]), int(n_iter),
+                               _p(H) if hist else ctypes.POINTER(ctypes.c_double)())
+        assert rc == 0
+        return H
+
+    def run(self, n_iter: int, hist: bool = False):
+        st = self.zero_state()
+        H = self.iterate(st, n_iter, hist)
+        return st, H
+
+    def solve(self, b: np.ndarray) -> np.ndarray:
+        """Step I alone: X = Q^-1 b, with b the full right-hand side of Eq. matB."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        X = np.empty_like(b)
+        rc = lib().orc_solve(*self._hdr(), _p(self.hre), _p(self.him), _p(b), _p(X))
+        assert rc == 0
+        return X
+
+    def make_b(self, st: dict) -> np.ndarray:
+        """Eq. matB from a state."""
+        b = np.empty((self.L, self.N, self.N))
+        rc = lib().orc_make_b(*self._hdr(), _p(self.HtY), _p(st["P"]), _p(st["T"]), _p(st["S"]),
+                              _p(st["GP"]), _p(st["GT"]), _p(st["GS"]), _p(b))
+        assert rc == 0
+        return b
+
+    def primal_dual(self, X: np.ndarray, st: dict) -> None:
+        """Steps II-VI in place on `st` for a given new X (st['X'] is set to X)."""
+        st["X"][...] = X
+        rc = lib().orc_primal_dual(*self._hdr(), _p(st["X"]), _p(st["P"]), _p(st["T"]),
+                                   _p(st["V"]), _p(st["S"]), _p(st["GP"]), _p(st["GT"]),
+                                   _p(st["GV"]), _p(st["GS"]))
+        assert rc == 0
