@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark of the spatio-spectral ADMM iteration (arXiv:1504.06847, Algorithm 1).
+
+One step = one full ADMM iteration (steps I-VI: FFT X-solve, positivity,
+wavelet and DCT soft-thresholds, S update, duals) over the 1024 x 1024 x 64
+synthetic cube, through the C ABI.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU runs (torchrun, one rank per GPU) solve one independent replica of
+the cube per rank (the path has no exchange between cubes): weak scaling.
+The reference arm (--impl reference) times the FP64 CPU oracle on the host
+cores instead, on a 256 x 256 x 64 sample of the same workload recipe.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("ADMM voxel-iterations/sec at 1024²×64 bands and % HBM roofline, "
+          "FP32/split-BF16 vs FP64")
+UNIT = "voxel-it/s"
+WORKLOAD = "1024x1024x64"
+SAMPLE = dict(N=256, L=64, n_sources=19, n_antennas=512, seed=3, point_frac=0.2)
+SAMPLE_NAME = "256x256x64 cube from the same recipe (seed 3, 19 sources, 512 antennas)"
+FALLBACK_HBM_GBS = 6800.0
+# Minimum HBM bytes per voxel-iteration of the whole step (FP32, 8 distinct bases):
+# 12 persistent arrays read+written (96 B), X (12 B), b (16 B), FFT intermediates (16 B),
+# Fourier constants (6 B).
+STEP_ALG_BYTES_PER_VOXEL = 146.0
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each kernel at the
+# benchmark workload, from profiles/ (None where no capture of the current kernel exists).
+NCU_TRAFFIC_PER_LAUNCH = {}
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def alg_bytes_per_iteration(N, L, nd=8, J=3, esz=4):
+    """Algorithmic HBM bytes of each kernel class over one iteration (sum of its launches)."""
+    V = N * N * L
+    out = {
+        "rows_fwd": 2 * V * esz,                      # b in, packed half spectrum out
+        "cols_solve": 3.5 * V * esz,                  # spectrum in/out, c (complex), g (real)
+        "rows_inv": 2 * V * esz,                      # spectrum in, X out
+        "spectral": 10 * V * esz,                     # X; Gamma_P, S, Gamma_V, Gamma_S in/out; b out
+    }
+    ll = 0.0
+    for j in range(1, J):
+        src = V if j == 1 else nd * V / 4 ** (j - 1)
+        ll += (src + nd * V / 4 ** j) * esz
+    out["wav_ll"] = ll
+    lvl1 = (V + 2 * V + 2 * nd * (0.75 if J > 1 else 1.0) * V + (nd * V / 4 if J > 1 else 0)) * esz
+    out["wav_level1"] = lvl1
+    lj = 0.0
+    for j in range(2, J + 1):
+        size = V / 4 ** (j - 1)
+        coarsest = j == J
+        lj += (nd * size + 2 * nd * (1.0 if coarsest else 0.75) * size + (0 if coarsest else nd * size / 4)
+               + nd * size) * esz
+    out["wav_levelj"] = lj
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        if shutil.which("nvidia-smi") is None:
+            return self
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits", "-lms", "200"],
+                                     stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def cpu_baseline(seconds=15.0):
+    """The FP64 oracle as it stands, on every host core this process may use."""
+    cores = len(os.sched_getaffinity(0))
+    os.environ["OMP_NUM_THREADS"] = str(cores)
+    import oracle
+    from paper_1504_06847_gb300 import synth
+
+    c = synth.make_cube(**SAMPLE)
+    pb = oracle.Problem(c.psf, c.y, synth.WORKLOAD_PARAMS)
+    st = pb.zero_state()
+    pb.iterate(st, 1)  # warm-up
+    n, t0 = 0, time.perf_counter()
+    while True:
+        pb.iterate(st, 1)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or n >= 200:
+            break
+    V = SAMPLE["N"] ** 2 * SAMPLE["L"]
+    return {"value": V * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} FP64 Algorithm-1 iterations of the {SAMPLE_NAME} ({el:.1f} s)"}
+
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    cores = len(os.sched_getaffinity(0))
+    os.environ["OMP_NUM_THREADS"] = str(cores)
+    import oracle
+    from paper_1504_06847_gb300 import synth
+
+    c = synth.make_cube(**SAMPLE)
+    pb = oracle.Problem(c.psf, c.y, synth.WORKLOAD_PARAMS)
+    st = pb.zero_state()
+    for _ in range(args.warmup):
+        pb.iterate(st, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pb.iterate(st, 1)
+    el = time.perf_counter() - t0
+    V = SAMPLE["N"] ** 2 * SAMPLE["L"]
+    value = V * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": SAMPLE_NAME, "n_iter_per_step": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"one FP64 Algorithm-1 iteration of the {SAMPLE_NAME} per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_1504_06847_gb300 as mf
+    from paper_1504_06847_gb300 import synth
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    cube = synth.workload(WORKLOAD)
+    N, L = cube.y.shape[-1], cube.y.shape[0]
+    V = N * N * L
+    prm = synth.WORKLOAD_PARAMS
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        psf = torch.tensor(cube.psf, dtype=torch.float32, device="cuda")
+        y = torch.tensor(cube.y, dtype=torch.float32, device="cuda")
+        plan = mf.Plan(psf)
+        params = plan.params(stream=stream.cuda_stream, **prm)
+        params_warm = plan.params(stream=stream.cuda_stream, warm_start=1, **prm)
+        plan.iterate(y, args.warmup, params)
+    stream.synchronize()
+
+    # --- device-timed region: K iterations, inputs resident in HBM (working set >> L2) ---
+    plan.set_timing(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        plan.iterate(y, args.steps, params_warm)
+        ev1.record(stream)
+        stream.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    timing = plan.timing()
+    plan.set_timing(False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * V * args.steps / (ms * 1e-3)
+    launches = sum(n for _, n in timing.values())
+
+    # --- end to end through the C ABI with host buffers: each step copies y from
+    # pinned host memory, runs one iteration with the FP64 residual report, reads it back ---
+    y_host = torch.tensor(cube.y, dtype=torch.float32).pin_memory()
+    y_dev = torch.empty_like(y)
+    params_e2e = plan.params(stream=stream.cuda_stream, warm_start=1, resid_every=1, **prm)
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            y_dev.copy_(y_host, non_blocking=True)
+        plan.iterate(y_dev, 1, params_e2e)
+        rep = plan.report()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * V * e2e_steps / e2e_s
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # --- roofline of the dominant kernel (device time from the live CUDA events) ---
+    peak, peak_kind = measured_peak()
+    alg = alg_bytes_per_iteration(N, L)
+    per_kernel = {}
+    for name, (kms, n) in timing.items():
+        if n == 0:
+            continue
+        d = {"ms_total": kms, "launches": n, "ms_per_launch": kms / n}
+        if name in alg and kms > 0:
+            d["achieved_gbs"] = alg[name] * args.steps / (kms * 1e-3) / 1e9
+        per_kernel[name] = d
+    dom = max((k for k in per_kernel if k in alg), key=lambda k: per_kernel[k]["ms_total"])
+    dk = per_kernel[dom]
+    launches_per_iter = dk["launches"] / args.steps
+    ach = dk["achieved_gbs"]
+    traffic = NCU_TRAFFIC_PER_LAUNCH.get(dom)
+    roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": traffic, "kernel": dom, "peak_kind": f"{peak_kind} copy bandwidth",
+                "alg_bytes_per_launch": alg[dom] / launches_per_iter,
+                "ms_per_launch": dk["ms_per_launch"]}
+    step_ach = STEP_ALG_BYTES_PER_VOXEL * V / (ms / args.steps * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "L": L, "wavelet_levels": 3, "bases": "Db1-Db8+Haar",
+                   "n_iter_per_step": 1, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": f"inputs larger than L2 (plan working set {plan.device_bytes / 1e9:.1f} GB)",
+                   "params": prm},
+        "roofline": roofline,
+        "step_roofline": {"bound": "hbm", "alg_bytes_per_voxel": STEP_ALG_BYTES_PER_VOXEL, "achieved": step_ach,
+                          "peak": peak, "unit": "GB/s", "frac": step_ach / peak},
+        "kernels": per_kernel,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(y_host.numel() * 4),
+                "d2h_bytes_per_step": 16 * 8, "steps": e2e_steps,
+                "note": "per step: pinned y upload, one iteration with FP64 residuals, report read-back"},
+    }
+    line["clocks"] = clk.summary()
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

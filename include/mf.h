@@ -1,0 +1,169 @@
+/*
+ * mf.h -- C ABI of the GB300 (sm_103a) spatio-spectral ADMM deconvolution
+ * (Ferrari et al., arXiv:1504.06847, "Multi-frequency image reconstruction
+ * for radio interferometry. A regularized inverse problem approach").
+ *
+ * Problem (Section 2, Eqs. nbmodel, wbmodel, costreg, eq:RegAll):
+ *   y_l = H_l x_l + n_l for every band l = 0..L-1, H_l the circular
+ *   convolution by band l's PSF, and
+ *   min_X 1/2 ||Y - H X||^2 + 1_{R+}(X) + mu_eps/2 ||X||_F^2
+ *         + mu_s ||W_s X||_1 + mu_nu ||X W_nu||_1,
+ * solved by the ADMM of Section 3 (Algorithm 1, steps I-VI) with
+ *   W_s  = union of orthonormal periodic 2-D wavelet bases (Db1..Db8 and Haar,
+ *          Section 4), J levels of the separable Mallat transform;
+ *   W_nu = orthonormal DCT-II along the band axis (Section 4), m_nu = 1;
+ *   step I solved with the Fourier filter (|h_l|^2 + rho)^-1 (Section 3,
+ *          Eq. Qlsimp, rho = mu_eps + rho_S + rho_P + n_s rho_T).
+ *
+ * Conventions shared by every entry point:
+ *   - Cubes are [L][N][N] row-major (band images contiguous; a pixel spectrum
+ *     has stride N*N), in the plan's real type (float, or double for the
+ *     *_f64 plans).  Unless stated otherwise pointers are DEVICE pointers of
+ *     the current CUDA device.
+ *   - PSF: each band's PSF has its peak at pixel (N/2, N/2); the operator is
+ *     (H x)[i] = sum_j psf[(i - j + N/2) mod N] x[j] in 2-D (circular), and H^T
+ *     uses the conjugate transfer function.
+ *   - N must be a power of two in [16, 2048]; L in [2, 128].  The wavelet
+ *     levels J >= 1 with N / 2^J >= 2.
+ *   - Asynchrony: iterate calls enqueue work on params->stream and return;
+ *     the first error is latched in the plan and returned by later calls.
+ *   - No C++ exception crosses this interface.
+ */
+#ifndef MF_H
+#define MF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mf_plan mf_plan;
+
+typedef enum {
+  MF_OK = 0,
+  MF_ERR_INVALID = 1,   /* bad argument; nothing was enqueued */
+  MF_ERR_OOM = 2,       /* device allocation failed */
+  MF_ERR_CUDA = 3,      /* a CUDA call or launch failed */
+  MF_ERR_TIMEOUT = 4,   /* a bounded device wait expired */
+  MF_ERR_NONFINITE = 5  /* a NaN/Inf was seen by a residual reduction */
+} mf_status;
+
+typedef enum {
+  MF_FP32 = 0,                 /* FP32 cube, FP32 DCT */
+  MF_FP64 = 1,                 /* FP64 plan (created with mf_plan_create_f64) */
+  MF_FP32_DCT_SPLITBF16 = 2    /* FP32 cube, DCT as split-BF16 tensor-core products */
+} mf_precision;
+
+/* Regularisation and penalty parameters (Section 3 and the settings of Section 4). */
+typedef struct {
+  double mu_eps, mu_s, mu_nu;        /* mu_epsilon, mu_s, mu_nu (Eq. eq:RegAll) */
+  double rho_P, rho_T, rho_V, rho_S; /* augmented Lagrangian penalties (Eqs. admm1/admm2) */
+  int wavelet_levels;                /* J (default 3) */
+  unsigned wavelet_mask;             /* bit K-1: DbK (K = 1..8); bit 8: Haar. default 0x1FF */
+  int precision;                     /* mf_precision */
+  int resid_every;                   /* 0: never; k: FP64 residuals/objective every k-th iteration
+                                        and on the last one */
+  int warm_start;                    /* 0: zero state first (Algorithm 1); 1: continue */
+  void* stream;                      /* cudaStream_t; NULL = legacy default stream */
+} mf_params;
+
+/* Filled by mf_plan_get_report, FP64 sums over the cube, measured after the
+ * dual update of the last residual iteration:
+ *   primal_res = ||P-X||^2 + ||T-W_s X||^2 + ||V-S W_nu||^2 + ||S-X||^2
+ *              = sum_c ||dGamma_c||^2 / rho_c^2 (Boyd et al. 2011, Sec. 3.3);
+ *   objective  = 1/2||Y-HX||^2 + mu_eps/2||X||^2 + mu_s||W_s X||_1 + mu_nu||X W_nu||_1;
+ *   x_min      = min(X) (X may carry small negatives; P is its projection). */
+typedef struct {
+  int iters_done;
+  int resid_iter;      /* iteration index the residual fields refer to (-1: none) */
+  double primal_res;
+  double dual_gamma;   /* sum_c ||dGamma_c||^2 (unweighted) */
+  double objective;
+  double x_min;
+  double x_norm2;
+} mf_report;
+
+/* Defaults: mu_eps 0.001, mu_s 0.05, mu_nu 0.01, all rho 1, J 3, mask 0x1FF,
+ * MF_FP32, resid_every 0, warm_start 0, stream NULL. */
+void mf_params_default(mf_params* p);
+
+/* Creates a plan for N x N x L cubes.  psf_cube: device [L][N][N] float; it is
+ * read during the call only (the plan keeps its transfer function).  On
+ * success *out owns all device memory of the plan (see mf_plan_device_bytes).
+ * Errors: MF_ERR_INVALID (sizes, NULL), MF_ERR_OOM, MF_ERR_CUDA. */
+mf_status mf_plan_create(int N, int L, const float* psf_cube, mf_plan** out);
+/* Same with an FP64 plan (all cubes double). */
+mf_status mf_plan_create_f64(int N, int L, const double* psf_cube, mf_plan** out);
+/* Frees everything the plan owns; NULL is a no-op.  Synchronises the device. */
+void mf_plan_destroy(mf_plan* p);
+size_t mf_plan_device_bytes(const mf_plan* p);
+
+/* Runs n_iter >= 1 iterations of Algorithm 1 on the dirty cube y_cube
+ * (device [L][N][N] float, read during the enqueued work).  Constants
+ * H^T y and the Fourier filter are recomputed on every call.  Returns
+ * MF_ERR_INVALID for bad parameters (rho <= 0, mu < 0, J, mask, precision
+ * not matching the plan), otherwise the plan's latched status. */
+mf_status mf_admm_iterate(mf_plan* p, const float* y_cube, const mf_params* prm, int n_iter);
+mf_status mf_admm_iterate_f64(mf_plan* p, const double* y_cube, const mf_params* prm, int n_iter);
+
+/* Which state array to read or write (all [L][N][N] unless noted). */
+typedef enum {
+  MF_ARR_X = 0,        /* X after the last step I (Algorithm 1 returns X) */
+  MF_ARR_GAMMA_P = 1,  /* Gamma_P */
+  MF_ARR_S_DCT = 2,    /* S W_nu: S in the DCT domain (row k = DCT frequency) */
+  MF_ARR_GAMMA_V = 3,  /* Gamma_V (DCT domain) */
+  MF_ARR_GAMMA_S_DCT = 4, /* Gamma_S W_nu */
+  MF_ARR_B = 5,        /* right-hand side of Eq. matB without the H^T Y term */
+  MF_ARR_GAMMA_T = 6   /* Gamma_T: [nd][L][N][N], nd distinct bases in mask order
+                          (Db1..Db8, Haar folded into Db1 when both are on),
+                          each band in the in-place Mallat layout */
+} mf_array;
+
+/* Device-to-device copies of a state array (dst/src: device, plan's real
+ * type).  *count receives the element count when dst is NULL.  These calls
+ * synchronise the plan's last stream. */
+mf_status mf_plan_get_array(mf_plan* p, int which, void* dst, size_t* count);
+mf_status mf_plan_set_array(mf_plan* p, int which, const void* src, size_t count);
+
+/* Whole ADMM state (every array above) as one opaque device buffer for
+ * checkpoint and warm restart.  With buf == NULL *bytes receives the size. */
+mf_status mf_plan_get_state(mf_plan* p, void* buf, size_t* bytes);
+mf_status mf_plan_set_state(mf_plan* p, const void* buf, size_t bytes);
+
+/* Synchronises the plan's stream and fills *r.  Returns the latched status. */
+mf_status mf_plan_get_report(mf_plan* p, mf_report* r);
+
+/* Kernels of one iteration, for per-kernel timing and launch counts. */
+typedef enum {
+  MF_K_ROWS_FWD = 0,   /* step I: forward row FFT of b */
+  MF_K_COLS = 1,       /* step I: column FFT, Fourier-diagonal divide, inverse column FFT */
+  MF_K_ROWS_INV = 2,   /* step I: inverse row FFT into X */
+  MF_K_SPECTRAL = 3,   /* steps II, IV, V and their duals, pointwise part of b */
+  MF_K_WAV_LL = 4,     /* step III: low-low analysis of the coarser levels */
+  MF_K_WAV_LEVEL1 = 5, /* step III: finest level, every basis, adds into b */
+  MF_K_WAV_LEVELJ = 6, /* step III: coarser fused levels */
+  MF_K_SETUP = 7,      /* per-call constants: F(y), g, c; zeroing of the state */
+  MF_K_REDUCE = 8,     /* FP64 fold of the residual partials */
+  MF_K_COUNT = 9
+} mf_kernel;
+
+/* Per-kernel CUDA-event timing of the plan's launches on its stream (off by
+ * default; each timed launch is bracketed by two events).  Enabling resets the
+ * accumulators.  mf_plan_get_timing synchronises the stream and returns, for
+ * one kernel, the summed duration in ms (0 when timing is off) and the launch
+ * count (always counted since the plan was created or timing was enabled). */
+mf_status mf_plan_set_timing(mf_plan* p, int enable);
+mf_status mf_plan_get_timing(mf_plan* p, int kernel, double* total_ms, long long* launches);
+const char* mf_kernel_name(int kernel);
+
+/* Host copy of the library's low-pass filter DbK (K = 1..8, 2K taps, double),
+ * built at load time from Daubechies' spectral factorisation. */
+mf_status mf_wavelet_filter(int K, double* taps_host, int* len);
+
+const char* mf_status_string(mf_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MF_H */

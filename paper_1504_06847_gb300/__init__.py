@@ -1,0 +1,245 @@
+"""GB300 (sm_103a) spatio-spectral ADMM deconvolution (arXiv:1504.06847).
+
+Thin ctypes binding of the C ABI in ``include/mf.h``.  Every step of the
+iteration runs in the library's CUDA kernels; PyTorch only provides device
+memory (tensors whose pointers are passed through) and streams.  There is no
+CPU fallback: importing the binding without the built library raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmf.so")
+
+MF_OK, MF_ERR_INVALID, MF_ERR_OOM, MF_ERR_CUDA, MF_ERR_TIMEOUT, MF_ERR_NONFINITE = range(6)
+MF_FP32, MF_FP64, MF_FP32_DCT_SPLITBF16 = range(3)
+ARR_X, ARR_GAMMA_P, ARR_S_DCT, ARR_GAMMA_V, ARR_GAMMA_S_DCT, ARR_B, ARR_GAMMA_T = range(7)
+
+EXPORTS = ["mf_params_default", "mf_plan_create", "mf_plan_create_f64", "mf_plan_destroy",
+           "mf_plan_device_bytes", "mf_admm_iterate", "mf_admm_iterate_f64", "mf_plan_get_array",
+           "mf_plan_set_array", "mf_plan_get_state", "mf_plan_set_state", "mf_plan_get_report",
+           "mf_wavelet_filter", "mf_status_string", "mf_plan_set_timing", "mf_plan_get_timing",
+           "mf_kernel_name"]
+
+KERNELS = ["rows_fwd", "cols_solve", "rows_inv", "spectral", "wav_ll", "wav_level1", "wav_levelj", "setup",
+           "reduce"]
+
+
+class MFError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("mu_eps", ctypes.c_double), ("mu_s", ctypes.c_double), ("mu_nu", ctypes.c_double),
+                ("rho_P", ctypes.c_double), ("rho_T", ctypes.c_double), ("rho_V", ctypes.c_double),
+                ("rho_S", ctypes.c_double), ("wavelet_levels", ctypes.c_int),
+                ("wavelet_mask", ctypes.c_uint), ("precision", ctypes.c_int),
+                ("resid_every", ctypes.c_int), ("warm_start", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("iters_done", ctypes.c_int), ("resid_iter", ctypes.c_int),
+                ("primal_res", ctypes.c_double), ("dual_gamma", ctypes.c_double),
+                ("objective", ctypes.c_double), ("x_min", ctypes.c_double),
+                ("x_norm2", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libmf.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, sz = ctypes.c_void_p, ctypes.c_size_t
+        L.mf_params_default.argtypes = [ctypes.POINTER(Params)]
+        L.mf_params_default.restype = None
+        for name in ("mf_plan_create", "mf_plan_create_f64"):
+            f = getattr(L, name)
+            f.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(vp)]
+            f.restype = ctypes.c_int
+        L.mf_plan_destroy.argtypes = [vp]
+        L.mf_plan_destroy.restype = None
+        L.mf_plan_device_bytes.argtypes = [vp]
+        L.mf_plan_device_bytes.restype = sz
+        for name in ("mf_admm_iterate", "mf_admm_iterate_f64"):
+            f = getattr(L, name)
+            f.argtypes = [vp, vp, ctypes.POINTER(Params), ctypes.c_int]
+            f.restype = ctypes.c_int
+        L.mf_plan_get_array.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(sz)]
+        L.mf_plan_get_array.restype = ctypes.c_int
+        L.mf_plan_set_array.argtypes = [vp, ctypes.c_int, vp, sz]
+        L.mf_plan_set_array.restype = ctypes.c_int
+        L.mf_plan_get_state.argtypes = [vp, vp, ctypes.POINTER(sz)]
+        L.mf_plan_get_state.restype = ctypes.c_int
+        L.mf_plan_set_state.argtypes = [vp, vp, sz]
+        L.mf_plan_set_state.restype = ctypes.c_int
+        L.mf_plan_get_report.argtypes = [vp, ctypes.POINTER(Report)]
+        L.mf_plan_get_report.restype = ctypes.c_int
+        L.mf_wavelet_filter.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+        L.mf_wavelet_filter.restype = ctypes.c_int
+        L.mf_status_string.argtypes = [ctypes.c_int]
+        L.mf_status_string.restype = ctypes.c_char_p
+        L.mf_plan_set_timing.argtypes = [vp, ctypes.c_int]
+        L.mf_plan_set_timing.restype = ctypes.c_int
+        L.mf_plan_get_timing.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_longlong)]
+        L.mf_plan_get_timing.restype = ctypes.c_int
+        L.mf_kernel_name.argtypes = [ctypes.c_int]
+        L.mf_kernel_name.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return lib().mf_status_string(int(s)).decode()
+
+
+def _check(rc, what):
+    if rc != MF_OK:
+        raise MFError(rc, what)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().mf_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def wavelet_filter(K: int):
+    """The library's DbK low-pass taps (host doubles)."""
+    taps = (ctypes.c_double * 16)()
+    n = ctypes.c_int()
+    _check(lib().mf_wavelet_filter(K, taps, ctypes.byref(n)), "mf_wavelet_filter")
+    return [taps[i] for i in range(n.value)]
+
+
+class Plan:
+    """A plan for N x N x L cubes on the current CUDA device.
+
+    psf: CUDA tensor [L, N, N] (float32, or float64 for an FP64 plan).
+    """
+
+    def __init__(self, psf):
+        import torch
+
+        if not psf.is_cuda or psf.dim() != 3 or psf.shape[1] != psf.shape[2]:
+            raise ValueError("psf must be a CUDA tensor [L, N, N]")
+        self.dtype = psf.dtype
+        if self.dtype not in (torch.float32, torch.float64):
+            raise ValueError("psf must be float32 or float64")
+        self.L, self.N = int(psf.shape[0]), int(psf.shape[1])
+        psf = psf.contiguous()
+        h = ctypes.c_void_p()
+        create = lib().mf_plan_create if self.dtype == torch.float32 else lib().mf_plan_create_f64
+        _check(create(self.N, self.L, ctypes.c_void_p(psf.data_ptr()), ctypes.byref(h)), "mf_plan_create")
+        self._h = h
+        self.device = psf.device
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().mf_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def device_bytes(self) -> int:
+        return int(lib().mf_plan_device_bytes(self._h))
+
+    def params(self, **kw) -> Params:
+        import torch
+
+        kw.setdefault("precision", MF_FP32 if self.dtype == torch.float32 else MF_FP64)
+        if "stream" not in kw:
+            kw["stream"] = torch.cuda.current_stream(self.device).cuda_stream
+        return default_params(**kw)
+
+    def iterate(self, y, n_iter: int, params: Params | None = None, **kw):
+        """Enqueues n_iter ADMM iterations on y (CUDA tensor [L, N, N]) and returns.
+        A status latched by earlier asynchronous work raises here."""
+        import torch
+
+        if params is None:
+            params = self.params(**kw)
+        if y.dtype != self.dtype or not y.is_cuda or tuple(y.shape) != (self.L, self.N, self.N):
+            raise ValueError("y must be a CUDA tensor [L, N, N] of the plan's dtype")
+        y = y.contiguous()
+        f = lib().mf_admm_iterate if self.dtype == torch.float32 else lib().mf_admm_iterate_f64
+        _check(f(self._h, ctypes.c_void_p(y.data_ptr()), ctypes.byref(params), int(n_iter)), "mf_admm_iterate")
+        self._y_keepalive = y
+
+    def get(self, which: int):
+        import torch
+
+        n = ctypes.c_size_t()
+        _check(lib().mf_plan_get_array(self._h, which, None, ctypes.byref(n)), "mf_plan_get_array")
+        out = torch.empty(n.value, dtype=self.dtype, device=self.device)
+        _check(lib().mf_plan_get_array(self._h, which, ctypes.c_void_p(out.data_ptr()), ctypes.byref(n)),
+               "mf_plan_get_array")
+        if which == ARR_GAMMA_T:
+            return out.view(-1, self.L, self.N, self.N)
+        return out.view(self.L, self.N, self.N)
+
+    def set(self, which: int, t):
+        t = t.contiguous()
+        _check(lib().mf_plan_set_array(self._h, which, ctypes.c_void_p(t.data_ptr()), t.numel()),
+               "mf_plan_set_array")
+
+    def x(self):
+        return self.get(ARR_X)
+
+    def report(self) -> dict:
+        r = Report()
+        rc = lib().mf_plan_get_report(self._h, ctypes.byref(r))
+        d = r.as_dict()
+        d["status"] = rc
+        return d
+
+    def set_timing(self, enable: bool):
+        """Per-kernel CUDA-event timing on the plan's stream (resets the counters)."""
+        _check(lib().mf_plan_set_timing(self._h, int(bool(enable))), "mf_plan_set_timing")
+
+    def timing(self) -> dict:
+        """{kernel name: (total ms, launches)} since timing was last set."""
+        out = {}
+        for k, name in enumerate(KERNELS):
+            ms = ctypes.c_double()
+            n = ctypes.c_longlong()
+            _check(lib().mf_plan_get_timing(self._h, k, ctypes.byref(ms), ctypes.byref(n)), "mf_plan_get_timing")
+            out[name] = (ms.value, n.value)
+        return out
+
+    def get_state(self):
+        import torch
+
+        n = ctypes.c_size_t()
+        _check(lib().mf_plan_get_state(self._h, None, ctypes.byref(n)), "mf_plan_get_state")
+        buf = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+        _check(lib().mf_plan_get_state(self._h, ctypes.c_void_p(buf.data_ptr()), ctypes.byref(n)),
+               "mf_plan_get_state")
+        return buf
+
+    def set_state(self, buf):
+        _check(lib().mf_plan_set_state(self._h, ctypes.c_void_p(buf.data_ptr()), buf.numel()),
+               "mf_plan_set_state")

@@ -1,0 +1,156 @@
+// Internal declarations of the mf library: plan layout, kernel parameter
+// blocks and the host launchers of each kernel family.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+#include <vector>
+
+#include "../../include/mf.h"
+
+#define MF_MAX_K 8        // DbK with K <= 8 (Db1..Db8 of the paper's dictionary)
+#define MF_MAX_F 16       // 2 * MF_MAX_K taps
+#define MF_MAX_BASES 8    // distinct wavelet bases (Haar folds into Db1)
+#define MF_MAX_LEVELS 8
+#define MF_MAX_L 128
+#define MF_NQ 16          // reduction quantities per block partial
+
+namespace mf {
+
+const double* filter_taps(int K);  // DbK low-pass, 2K taps (daub.cpp)
+
+template <class R> struct cx_t;
+template <> struct cx_t<float> { typedef float2 type; };
+template <> struct cx_t<double> { typedef double2 type; };
+template <class R> using cx = typename cx_t<R>::type;
+
+// Distinct bases of W_s as seen by the kernels: filter half-length K,
+// synthesis weight w (2 when Db1 and Haar are both selected), taps.
+template <class R>
+struct WavSet {
+  int nd;
+  int K[MF_MAX_BASES];
+  R w[MF_MAX_BASES];
+  R h[MF_MAX_BASES][MF_MAX_F];
+  R g[MF_MAX_BASES][MF_MAX_F];
+};
+
+// Scalars of one ADMM iteration.
+template <class R>
+struct IterScalars {
+  R rho_P, rho_T, rho_V, rho_S;
+  R tau_T, tau_V;   // mu_s / rho_T, mu_nu / rho_V
+  R inv_rho_P, inv_rho_T, inv_rho_V, inv_VS;  // 1/rho_P, 1/rho_T, 1/rho_V, 1/(m_nu rho_V + rho_S)
+};
+
+// Reduction slots of the per-block FP64 partials.
+enum {
+  Q_DGP = 0,   // ||dGamma_P||^2
+  Q_DGT,       // ||dGamma_T||^2 (all bases, weights included)
+  Q_DGV,       // ||dGamma_V||^2
+  Q_DGS,       // ||dGamma_S||^2
+  Q_X2,        // ||X||^2
+  Q_L1NU,      // ||X W_nu||_1
+  Q_L1S,       // ||W_s X||_1 (weights included)
+  Q_FIT,       // 1/2 ||Y - H X||^2
+  Q_XMIN,      // min X (reduced with min)
+  Q_NONFIN,    // count of non-finite values met
+  Q_COUNT
+};
+
+}  // namespace mf
+
+struct mf_plan {
+  int N, L, dbl;
+  size_t esz;        // sizeof real type
+  size_t cube;       // N * N * L elements
+  // ADMM state and work arrays (real type, [L][N][N] unless noted)
+  void* X;
+  void* b;
+  void* GP;
+  void* Sd;          // S W_nu
+  void* GV;          // Gamma_V
+  void* GSd;         // Gamma_S W_nu
+  void* GT[2];       // Gamma_T ping-pong, [MF_MAX_BASES][L][N][N]
+  int gt_cur;
+  int nd_state;      // distinct bases stored in GT (from the last iterate call)
+  void* work;        // packed half spectrum [L][N][N/2] complex
+  void* hhat;        // transfer function, unpacked half spectrum [L][N][N/2] complex
+  void* hhat_nyq;    // its kx = N/2 column [L][N] complex
+  void* yhat;        // F(y), same layout
+  void* yhat_nyq;
+  void* cc;          // conj(hhat) yhat g
+  void* cc_nyq;
+  void* gg;          // 1 / ((|hhat|^2 + rho) N^2), real [L][N][N/2]
+  void* gg_nyq;      // [L][N]
+  void* tw;          // exp(-2 pi i k / N), k < N, complex
+  void* dctC;        // L x L orthonormal DCT-II
+  void* scratch;     // wavelet LL_j and R_j images
+  size_t scratch_bytes;
+  double* partials;  // [max_blocks][MF_NQ]
+  size_t partial_cap;
+  double* sums;      // [MF_NQ] device
+  void* wset;        // WavSet of the current call (device)
+  size_t total_bytes;
+  cudaStream_t stream;
+  mf_status status;
+  int iters_done;
+  mf_report report;
+  int report_pending;   // sums on the device not yet folded into report
+  double rho_weights[4];
+  mf_params last_params;
+  // per-kernel timing
+  int timing;
+  long long launches[MF_K_COUNT];
+  double kernel_ms[MF_K_COUNT];
+  std::vector<cudaEvent_t> ev_pool;     // created events, reused
+  std::vector<int> ev_kernel;           // kernel id of each recorded pair
+  size_t ev_used;                       // events in use (2 per pair)
+};
+
+namespace mf {
+
+// ---- launchers (explicitly instantiated for float and double) ----
+// Row-wise forward real FFT of `rows` rows of length N: real in -> packed half spectrum out.
+template <class R> cudaError_t launch_rows_fwd(const R* in, cx<R>* out, int N, int rows, const cx<R>* tw, cudaStream_t s);
+// Column pass on the packed half spectrum of L bands.  mode 0: forward transform only,
+// unpacked into (out_main, out_nyq).  mode 1: forward, X = c + g B, inverse, in place.
+// mode 2: mode 1 plus the data-fit partials from (hh, yh).
+template <class R> cudaError_t launch_cols(cx<R>* work, int N, int L, const cx<R>* tw, int mode,
+                                           cx<R>* out_main, cx<R>* out_nyq,
+                                           const cx<R>* cc, const cx<R>* cc_nyq,
+                                           const R* gg, const R* gg_nyq,
+                                           const cx<R>* hh, const cx<R>* hh_nyq,
+                                           const cx<R>* yh, const cx<R>* yh_nyq, double* partials,
+                                           cudaStream_t s);
+template <class R> int cols_blocks(int N, int L);
+// Row-wise inverse: packed half spectrum in -> real rows out (scaled by N).
+template <class R> cudaError_t launch_rows_inv(const cx<R>* in, R* out, int N, int rows, const cx<R>* tw, cudaStream_t s);
+// g and c of the Fourier-diagonal solve.
+template <class R> cudaError_t launch_constants(const cx<R>* hh, const cx<R>* hh_nyq, const cx<R>* yh,
+                                                const cx<R>* yh_nyq, cx<R>* cc, cx<R>* cc_nyq, R* gg,
+                                                R* gg_nyq, int N, int L, double rho_bar, cudaStream_t s);
+
+// Spectral step (positivity, steps IV-V, duals, pointwise part of b).
+template <class R> cudaError_t launch_spectral(const R* X, R* GP, R* Sd, R* GV, R* GSd, R* b,
+                                               const R* dctC, int N, int L, IterScalars<R> sc,
+                                               double* partials, int resid, cudaStream_t s);
+template <class R> int spectral_blocks(int N, int L);
+
+// Wavelet analysis of the low-low band: LL_j (M/2 x M/2) from the M x M input.
+template <class R> cudaError_t launch_wav_ll(const R* in, size_t in_band_stride, size_t in_basis_stride,
+                                             R* out, int M, int L, int nd, const WavSet<R>* ws, cudaStream_t s);
+// Fused level: analysis of the M x M input, thresholds and dual update of the level's
+// coefficients, synthesis into the M x M output (or accumulation into b at level 1).
+template <class R> cudaError_t launch_wav_level(const R* in, size_t in_band_stride, size_t in_basis_stride,
+                                                const R* rcoarse, R* out, const R* gt_old, R* gt_new,
+                                                int N, int M, int L, int coarsest, int nd, const WavSet<R>* ws,
+                                                IterScalars<R> sc, double* partials, int resid,
+                                                cudaStream_t s);
+template <class R> int wav_level_blocks(int M, int L, int nd);
+
+cudaError_t launch_finalize(const double* partials, int nblocks, double* sums, int accumulate, cudaStream_t s);
+
+}  // namespace mf

@@ -1,0 +1,592 @@
+// C ABI of the library (include/mf.h): plans, the ADMM iteration of
+// Algorithm 1 as a fixed launch sequence on one stream, state access and the
+// FP64 residual report.
+//
+// One iteration (J wavelet levels, nd distinct bases):
+//   rows_fwd(b) -> cols(divide) -> rows_inv -> X                 step I
+//   spectral(X, Gamma_P, S, Gamma_V, Gamma_S) -> b               steps II, IV, V, VI
+//   wav_ll(j), j = 1..J-1; wav_level(j), j = J..1 -> b += ...    steps III, VI
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "mf_internal.cuh"
+
+using namespace mf;
+
+namespace {
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Brackets one launch with events when timing is on; counts launches always.
+struct Timed {
+  mf_plan* p;
+  int kid;
+  cudaStream_t s;
+  int n;
+  Timed(mf_plan* p_, int kid_, cudaStream_t s_, int launches = 1) : p(p_), kid(kid_), s(s_), n(launches) {
+    if (p->timing) record();
+  }
+  ~Timed() {
+    if (p->timing) record();
+    p->launches[kid] += n;
+  }
+  void record() {
+    if (p->ev_used == p->ev_pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        p->timing = 0;
+        return;
+      }
+      p->ev_pool.push_back(e);
+    }
+    cudaEventRecord(p->ev_pool[p->ev_used], s);
+    if ((p->ev_used & 1) == 0) p->ev_kernel.push_back(kid);
+    p->ev_used++;
+  }
+};
+
+void fold_timing(mf_plan* p) {
+  for (size_t i = 0; i + 1 < p->ev_used; i += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->ev_pool[i], p->ev_pool[i + 1]) == cudaSuccess)
+      p->kernel_ms[p->ev_kernel[i / 2]] += ms;
+    else
+      cudaGetLastError();
+  }
+  p->ev_used = 0;
+  p->ev_kernel.clear();
+}
+
+template <class R>
+__global__ void k_shift_psf(const R* __restrict__ psf, R* __restrict__ out, int N, size_t total) {
+  // out[l][r][c] = psf[l][(r + N/2) mod N][(c + N/2) mod N]: the peak moves to (0, 0)
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t NN = (size_t)N * N;
+    const size_t l = i / NN, rem = i % NN;
+    const int r = (int)(rem / N), c = (int)(rem % N);
+    out[i] = psf[l * NN + (size_t)((r + N / 2) & (N - 1)) * N + ((c + N / 2) & (N - 1))];
+  }
+}
+
+struct Alloc {
+  mf_plan* p;
+  bool ok = true;
+  void* get(size_t bytes) {
+    if (!ok) return nullptr;
+    void* d = nullptr;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) {
+      ok = false;
+      cudaGetLastError();
+      return nullptr;
+    }
+    p->total_bytes += bytes;
+    return d;
+  }
+};
+
+void free_plan_memory(mf_plan* p) {
+  void* ptrs[] = {p->X, p->b, p->GP, p->Sd, p->GV, p->GSd, p->GT[0], p->GT[1], p->work, p->hhat, p->hhat_nyq,
+                  p->yhat, p->yhat_nyq, p->cc, p->cc_nyq, p->gg, p->gg_nyq, p->tw, p->dctC, p->scratch,
+                  p->partials, p->sums, p->wset};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  p->ev_pool.clear();
+}
+
+size_t scratch_elems(int N, int L) {
+  // LL_j and R_j for j = 1..J-1 (J <= log2 N - 1), MF_MAX_BASES bases
+  size_t s = 0;
+  for (int M = N / 2; M >= 2; M /= 2) s += (size_t)M * M;
+  return 2 * s * MF_MAX_BASES * L;
+}
+
+template <class R>
+mf_status create(int N, int L, const R* psf, mf_plan** out) {
+  if (!out) return MF_ERR_INVALID;
+  *out = nullptr;
+  if (!psf || !is_pow2(N) || N < 16 || N > 2048 || L < 2 || L > MF_MAX_L) return MF_ERR_INVALID;
+  if (sizeof(R) == 8 && L > 64) return MF_ERR_INVALID;
+  mf_plan* p = new (std::nothrow) mf_plan();
+  if (!p) return MF_ERR_OOM;
+  p->N = N;
+  p->L = L;
+  p->dbl = sizeof(R) == 8;
+  p->esz = sizeof(R);
+  p->cube = (size_t)N * N * L;
+  p->report.resid_iter = -1;
+  const size_t cb = p->cube * sizeof(R);
+  const size_t half = (size_t)L * N * (N / 2) * sizeof(cx<R>);
+  const size_t nyq = (size_t)L * N * sizeof(cx<R>);
+  Alloc a{p};
+  p->X = a.get(cb);
+  p->b = a.get(cb);
+  p->GP = a.get(cb);
+  p->Sd = a.get(cb);
+  p->GV = a.get(cb);
+  p->GSd = a.get(cb);
+  p->GT[0] = a.get(cb * MF_MAX_BASES);
+  p->GT[1] = a.get(cb * MF_MAX_BASES);
+  p->work = a.get(half);
+  p->hhat = a.get(half);
+  p->hhat_nyq = a.get(nyq);
+  p->yhat = a.get(half);
+  p->yhat_nyq = a.get(nyq);
+  p->cc = a.get(half);
+  p->cc_nyq = a.get(nyq);
+  p->gg = a.get(half / 2);
+  p->gg_nyq = a.get(nyq / 2);
+  p->tw = a.get(sizeof(cx<R>) * N);
+  p->dctC = a.get(sizeof(R) * L * L);
+  p->scratch_bytes = scratch_elems(N, L) * sizeof(R);
+  p->scratch = a.get(p->scratch_bytes);
+  // partial rows: the largest grid of any kernel that reduces
+  size_t cap = (size_t)spectral_blocks<R>(N, L);
+  for (int M = N; M >= 4; M /= 2) {
+    const size_t nb = (size_t)wav_level_blocks<R>(M, L, M == N ? 1 : MF_MAX_BASES);
+    if (nb > cap) cap = nb;
+  }
+  const size_t colblocks = (size_t)L * N;  // upper bound of the column kernel's grid
+  if (colblocks > cap) cap = colblocks;
+  p->partial_cap = cap;
+  p->partials = (double*)a.get(cap * MF_NQ * sizeof(double));
+  p->sums = (double*)a.get(MF_NQ * sizeof(double));
+  p->wset = a.get(sizeof(WavSet<R>));
+  if (!a.ok) {
+    free_plan_memory(p);
+    delete p;
+    return MF_ERR_OOM;
+  }
+  // host-built tables: twiddles and the DCT-II matrix
+  {
+    cx<R>* tw = new cx<R>[N];
+    for (int k = 0; k < N; k++) {
+      const double ang = -2.0 * M_PI * (double)k / (double)N;
+      tw[k].x = (R)std::cos(ang);
+      tw[k].y = (R)std::sin(ang);
+    }
+    R* C = new R[(size_t)L * L];
+    for (int k = 0; k < L; k++) {
+      const double ak = k == 0 ? std::sqrt(1.0 / L) : std::sqrt(2.0 / L);
+      for (int l = 0; l < L; l++) C[k * L + l] = (R)(ak * std::cos(M_PI * (2.0 * l + 1.0) * k / (2.0 * L)));
+    }
+    cudaError_t e1 = cudaMemcpy(p->tw, tw, sizeof(cx<R>) * N, cudaMemcpyHostToDevice);
+    cudaError_t e2 = cudaMemcpy(p->dctC, C, sizeof(R) * L * L, cudaMemcpyHostToDevice);
+    delete[] tw;
+    delete[] C;
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      free_plan_memory(p);
+      delete p;
+      return MF_ERR_CUDA;
+    }
+  }
+  // transfer function of every band: F(ifftshift(psf))
+  R* shifted = reinterpret_cast<R*>(p->X);
+  k_shift_psf<R><<<1024, 256>>>(psf, shifted, N, p->cube);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_rows_fwd<R>(shifted, (cx<R>*)p->work, N, N * L, (const cx<R>*)p->tw, 0);
+  if (e == cudaSuccess)
+    e = launch_cols<R>((cx<R>*)p->work, N, L, (const cx<R>*)p->tw, 0, (cx<R>*)p->hhat, (cx<R>*)p->hhat_nyq,
+                       nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_plan_memory(p);
+    delete p;
+    return MF_ERR_CUDA;
+  }
+  *out = p;
+  return MF_OK;
+}
+
+mf_status check_params(const mf_plan* p, const mf_params* prm, int n_iter, int want_dbl) {
+  if (!p || !prm || n_iter < 1) return MF_ERR_INVALID;
+  if (p->dbl != want_dbl) return MF_ERR_INVALID;
+  if (!(prm->rho_P > 0 && prm->rho_T > 0 && prm->rho_V > 0 && prm->rho_S > 0)) return MF_ERR_INVALID;
+  if (!(prm->mu_eps >= 0 && prm->mu_s >= 0 && prm->mu_nu >= 0)) return MF_ERR_INVALID;
+  if (!std::isfinite(prm->mu_eps + prm->mu_s + prm->mu_nu + prm->rho_P + prm->rho_T + prm->rho_V + prm->rho_S))
+    return MF_ERR_INVALID;
+  const int J = prm->wavelet_levels;
+  if (J < 1 || (p->N >> J) < 2) return MF_ERR_INVALID;
+  if (prm->wavelet_mask == 0 || (prm->wavelet_mask >> 9) != 0) return MF_ERR_INVALID;
+  if (prm->resid_every < 0) return MF_ERR_INVALID;
+  if (p->dbl ? prm->precision != MF_FP64 : (prm->precision != MF_FP32)) return MF_ERR_INVALID;
+  return MF_OK;
+}
+
+// Distinct bases of the mask: Db1..Db8 in order, Haar folded into Db1 (weight 2)
+// or, without Db1, its own K = 1 entry.
+template <class R>
+WavSet<R> make_wavset(unsigned mask, int* n_s) {
+  WavSet<R> ws;
+  std::memset(&ws, 0, sizeof(ws));
+  int nd = 0, ns = 0;
+  for (int K = 1; K <= MF_MAX_K; K++) {
+    const bool on = (mask >> (K - 1)) & 1u;
+    const bool haar = (K == 1) && ((mask >> 8) & 1u);
+    if (!on && !haar) continue;
+    const double* h = filter_taps(K);
+    ws.K[nd] = K;
+    ws.w[nd] = (R)((on ? 1 : 0) + (haar ? 1 : 0));
+    for (int n = 0; n < 2 * K; n++) {
+      ws.h[nd][n] = (R)h[n];
+      const double gv = h[2 * K - 1 - n];
+      ws.g[nd][n] = (R)((n & 1) ? -gv : gv);
+    }
+    ns += (on ? 1 : 0) + (haar ? 1 : 0);
+    nd++;
+  }
+  ws.nd = nd;
+  *n_s = ns;
+  return ws;
+}
+
+template <class R>
+cudaError_t iteration(mf_plan* p, int J, int nd, const WavSet<R>* wsd, const IterScalars<R>& sc, int resid,
+                      cudaStream_t s) {
+  const int N = p->N, L = p->L;
+  const size_t NN = (size_t)N * N;
+  cudaError_t e;
+  // step I
+  {
+    Timed t(p, MF_K_ROWS_FWD, s);
+    if ((e = launch_rows_fwd<R>((const R*)p->b, (cx<R>*)p->work, N, N * L, (const cx<R>*)p->tw, s))) return e;
+  }
+  {
+    Timed t(p, MF_K_COLS, s);
+    if ((e = launch_cols<R>((cx<R>*)p->work, N, L, (const cx<R>*)p->tw, resid ? 2 : 1, nullptr, nullptr,
+                            (const cx<R>*)p->cc, (const cx<R>*)p->cc_nyq, (const R*)p->gg, (const R*)p->gg_nyq,
+                            (const cx<R>*)p->hhat, (const cx<R>*)p->hhat_nyq, (const cx<R>*)p->yhat,
+                            (const cx<R>*)p->yhat_nyq, p->partials, s)))
+      return e;
+  }
+  if (resid) {
+    Timed t(p, MF_K_REDUCE, s);
+    if ((e = launch_finalize(p->partials, cols_blocks<R>(N, L), p->sums, 0, s))) return e;
+  }
+  {
+    Timed t(p, MF_K_ROWS_INV, s);
+    if ((e = launch_rows_inv<R>((const cx<R>*)p->work, (R*)p->X, N, N * L, (const cx<R>*)p->tw, s))) return e;
+  }
+  // steps II, IV, V (+ duals), pointwise part of b
+  {
+    Timed t(p, MF_K_SPECTRAL, s);
+    if ((e = launch_spectral<R>((const R*)p->X, (R*)p->GP, (R*)p->Sd, (R*)p->GV, (R*)p->GSd, (R*)p->b,
+                                (const R*)p->dctC, N, L, sc, p->partials, resid, s)))
+      return e;
+  }
+  if (resid) {
+    Timed t(p, MF_K_REDUCE, s);
+    if ((e = launch_finalize(p->partials, spectral_blocks<R>(N, L), p->sums, 1, s))) return e;
+  }
+  // step III (+ dual), wavelet part of b
+  R* scr = (R*)p->scratch;
+  R* LL[MF_MAX_LEVELS + 1] = {nullptr};
+  R* RC[MF_MAX_LEVELS + 1] = {nullptr};
+  {
+    size_t off = 0;
+    for (int j = 1; j < J; j++) {
+      const size_t m = (size_t)(N >> j) * (N >> j) * MF_MAX_BASES * L;
+      LL[j] = scr + off;
+      off += m;
+      RC[j] = scr + off;
+      off += m;
+    }
+  }
+  for (int j = 1; j < J; j++) {
+    const int M = N >> (j - 1);
+    const R* in = j == 1 ? (const R*)p->X : LL[j - 1];
+    const size_t band_stride = j == 1 ? NN : (size_t)M * M;
+    const size_t basis_stride = j == 1 ? 0 : (size_t)M * M * L;
+    Timed t(p, MF_K_WAV_LL, s);
+    if ((e = launch_wav_ll<R>(in, band_stride, basis_stride, LL[j], M, L, nd, wsd, s))) return e;
+  }
+  const R* gto = (const R*)p->GT[p->gt_cur];
+  R* gtn = (R*)p->GT[1 - p->gt_cur];
+  for (int j = J; j >= 1; j--) {
+    const int M = N >> (j - 1);
+    const R* in = j == 1 ? (const R*)p->X : LL[j - 1];
+    const R* rco = j == J ? nullptr : RC[j];
+    R* outp = j == 1 ? (R*)p->b : RC[j - 1];
+    {
+      Timed t(p, j == 1 ? MF_K_WAV_LEVEL1 : MF_K_WAV_LEVELJ, s);
+      if ((e = launch_wav_level<R>(in, 0, 0, rco, outp, gto, gtn, N, M, L, j == J, nd, wsd, sc, p->partials,
+                                   resid, s)))
+        return e;
+    }
+    if (resid) {
+      Timed t(p, MF_K_REDUCE, s);
+      if ((e = launch_finalize(p->partials, wav_level_blocks<R>(M, L, M == N ? 1 : nd), p->sums, 1, s))) return e;
+    }
+  }
+  p->gt_cur = 1 - p->gt_cur;
+  return cudaSuccess;
+}
+
+template <class R>
+mf_status iterate(mf_plan* p, const R* y, const mf_params* prm, int n_iter) {
+  mf_status st = check_params(p, prm, n_iter, sizeof(R) == 8);
+  if (st != MF_OK) return st;
+  if (!y) return MF_ERR_INVALID;
+  if (p->status != MF_OK) return p->status;
+  cudaStream_t s = (cudaStream_t)prm->stream;
+  p->stream = s;
+  const int N = p->N, L = p->L;
+  int n_s = 0;
+  const WavSet<R> ws = make_wavset<R>(prm->wavelet_mask, &n_s);
+  const double rho_bar = prm->mu_eps + prm->rho_S + prm->rho_P + n_s * prm->rho_T;  // Eq. Qlsimp
+  IterScalars<R> sc;
+  sc.rho_P = (R)prm->rho_P;
+  sc.rho_T = (R)prm->rho_T;
+  sc.rho_V = (R)prm->rho_V;
+  sc.rho_S = (R)prm->rho_S;
+  sc.tau_T = (R)(prm->mu_s / prm->rho_T);
+  sc.tau_V = (R)(prm->mu_nu / prm->rho_V);
+  sc.inv_rho_P = (R)(1.0 / prm->rho_P);
+  sc.inv_rho_T = (R)(1.0 / prm->rho_T);
+  sc.inv_rho_V = (R)(1.0 / prm->rho_V);
+  sc.inv_VS = (R)(1.0 / (prm->rho_V + prm->rho_S));
+  if (prm->warm_start && p->nd_state != ws.nd && p->iters_done > 0)
+    return MF_ERR_INVALID;  // the stored Gamma_T belongs to another dictionary
+  cudaError_t e = cudaMemcpyAsync(p->wset, &ws, sizeof(ws), cudaMemcpyHostToDevice, s);
+  {
+    // constants: F(y), g, c
+    Timed t(p, MF_K_SETUP, s, 4);
+    if (!e) e = launch_rows_fwd<R>(y, (cx<R>*)p->work, N, N * L, (const cx<R>*)p->tw, s);
+    if (!e)
+      e = launch_cols<R>((cx<R>*)p->work, N, L, (const cx<R>*)p->tw, 0, (cx<R>*)p->yhat, (cx<R>*)p->yhat_nyq,
+                         nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, s);
+    if (!e)
+      e = launch_constants<R>((const cx<R>*)p->hhat, (const cx<R>*)p->hhat_nyq, (const cx<R>*)p->yhat,
+                              (const cx<R>*)p->yhat_nyq, (cx<R>*)p->cc, (cx<R>*)p->cc_nyq, (R*)p->gg,
+                              (R*)p->gg_nyq, N, L, rho_bar, s);
+    if (!e && !prm->warm_start) {
+      const size_t cb = p->cube * sizeof(R);
+      void* z[] = {p->X, p->b, p->GP, p->Sd, p->GV, p->GSd};
+      for (void* q : z)
+        if (!e) e = cudaMemsetAsync(q, 0, cb, s);
+      if (!e) e = cudaMemsetAsync(p->GT[p->gt_cur], 0, cb * MF_MAX_BASES, s);
+      p->iters_done = 0;
+      p->report.resid_iter = -1;
+    }
+  }
+  p->nd_state = ws.nd;
+  const int J = prm->wavelet_levels;
+  for (int it = 0; it < n_iter && !e; it++) {
+    const int resid = prm->resid_every > 0 && (((it + 1) % prm->resid_every) == 0 || it == n_iter - 1);
+    e = iteration<R>(p, J, ws.nd, (const WavSet<R>*)p->wset, sc, resid, s);
+    if (!e && resid) {
+      p->report_pending = 1;
+      p->report.resid_iter = p->iters_done + it + 1;
+    }
+  }
+  if (e) {
+    p->status = MF_ERR_CUDA;
+    return p->status;
+  }
+  p->iters_done += n_iter;
+  p->rho_weights[0] = prm->rho_P;
+  p->rho_weights[1] = prm->rho_T;
+  p->rho_weights[2] = prm->rho_V;
+  p->rho_weights[3] = prm->rho_S;
+  p->report.iters_done = p->iters_done;
+  std::memcpy(&p->last_params, prm, sizeof(mf_params));
+  return MF_OK;
+}
+
+void* array_ptr(mf_plan* p, int which, size_t* count) {
+  *count = p->cube;
+  switch (which) {
+    case MF_ARR_X: return p->X;
+    case MF_ARR_GAMMA_P: return p->GP;
+    case MF_ARR_S_DCT: return p->Sd;
+    case MF_ARR_GAMMA_V: return p->GV;
+    case MF_ARR_GAMMA_S_DCT: return p->GSd;
+    case MF_ARR_B: return p->b;
+    case MF_ARR_GAMMA_T: *count = p->cube * (p->nd_state > 0 ? p->nd_state : MF_MAX_BASES); return p->GT[p->gt_cur];
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void mf_params_default(mf_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->mu_eps = 0.001;
+  p->mu_s = 0.05;
+  p->mu_nu = 0.01;
+  p->rho_P = p->rho_T = p->rho_V = p->rho_S = 1.0;
+  p->wavelet_levels = 3;
+  p->wavelet_mask = 0x1FF;
+  p->precision = MF_FP32;
+}
+
+mf_status mf_plan_create(int N, int L, const float* psf_cube, mf_plan** out) {
+  return create<float>(N, L, psf_cube, out);
+}
+mf_status mf_plan_create_f64(int N, int L, const double* psf_cube, mf_plan** out) {
+  return create<double>(N, L, psf_cube, out);
+}
+
+void mf_plan_destroy(mf_plan* p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  free_plan_memory(p);
+  delete p;
+}
+
+size_t mf_plan_device_bytes(const mf_plan* p) { return p ? p->total_bytes : 0; }
+
+mf_status mf_admm_iterate(mf_plan* p, const float* y, const mf_params* prm, int n_iter) {
+  return iterate<float>(p, y, prm, n_iter);
+}
+mf_status mf_admm_iterate_f64(mf_plan* p, const double* y, const mf_params* prm, int n_iter) {
+  return iterate<double>(p, y, prm, n_iter);
+}
+
+mf_status mf_plan_get_array(mf_plan* p, int which, void* dst, size_t* count) {
+  if (!p) return MF_ERR_INVALID;
+  size_t n = 0;
+  void* src = array_ptr(p, which, &n);
+  if (!src) return MF_ERR_INVALID;
+  if (count) *count = n;
+  if (!dst) return count ? MF_OK : MF_ERR_INVALID;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return MF_ERR_CUDA;
+  if (cudaMemcpy(dst, src, n * p->esz, cudaMemcpyDeviceToDevice) != cudaSuccess) return MF_ERR_CUDA;
+  return MF_OK;
+}
+
+mf_status mf_plan_set_array(mf_plan* p, int which, const void* src, size_t count) {
+  if (!p || !src) return MF_ERR_INVALID;
+  size_t n = 0;
+  void* dst = array_ptr(p, which, &n);
+  if (which == MF_ARR_GAMMA_T) n = p->cube * MF_MAX_BASES;
+  if (!dst || count > n || (which != MF_ARR_GAMMA_T && count != n)) return MF_ERR_INVALID;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return MF_ERR_CUDA;
+  if (cudaMemcpy(dst, src, count * p->esz, cudaMemcpyDeviceToDevice) != cudaSuccess) return MF_ERR_CUDA;
+  if (which == MF_ARR_GAMMA_T) p->nd_state = (int)(count / p->cube);
+  return MF_OK;
+}
+
+mf_status mf_plan_get_state(mf_plan* p, void* buf, size_t* bytes) {
+  if (!p || !bytes) return MF_ERR_INVALID;
+  const size_t cb = p->cube * p->esz;
+  const size_t need = cb * (6 + MF_MAX_BASES);
+  if (!buf) {
+    *bytes = need;
+    return MF_OK;
+  }
+  if (*bytes < need) return MF_ERR_INVALID;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return MF_ERR_CUDA;
+  void* src[] = {p->X, p->b, p->GP, p->Sd, p->GV, p->GSd};
+  char* d = (char*)buf;
+  for (void* s : src) {
+    if (cudaMemcpy(d, s, cb, cudaMemcpyDeviceToDevice) != cudaSuccess) return MF_ERR_CUDA;
+    d += cb;
+  }
+  if (cudaMemcpy(d, p->GT[p->gt_cur], cb * MF_MAX_BASES, cudaMemcpyDeviceToDevice) != cudaSuccess)
+    return MF_ERR_CUDA;
+  return MF_OK;
+}
+
+mf_status mf_plan_set_state(mf_plan* p, const void* buf, size_t bytes) {
+  if (!p || !buf) return MF_ERR_INVALID;
+  const size_t cb = p->cube * p->esz;
+  if (bytes != cb * (6 + MF_MAX_BASES)) return MF_ERR_INVALID;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return MF_ERR_CUDA;
+  void* dst[] = {p->X, p->b, p->GP, p->Sd, p->GV, p->GSd};
+  const char* s = (const char*)buf;
+  for (void* d : dst) {
+    if (cudaMemcpy(d, s, cb, cudaMemcpyDeviceToDevice) != cudaSuccess) return MF_ERR_CUDA;
+    s += cb;
+  }
+  if (cudaMemcpy(p->GT[p->gt_cur], s, cb * MF_MAX_BASES, cudaMemcpyDeviceToDevice) != cudaSuccess)
+    return MF_ERR_CUDA;
+  if (p->iters_done == 0) p->iters_done = 1;
+  return MF_OK;
+}
+
+mf_status mf_plan_get_report(mf_plan* p, mf_report* r) {
+  if (!p || !r) return MF_ERR_INVALID;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) {
+    p->status = MF_ERR_CUDA;
+    return p->status;
+  }
+  if (p->report_pending) {
+    double q[MF_NQ];
+    if (cudaMemcpy(q, p->sums, sizeof(q), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      p->status = MF_ERR_CUDA;
+      return p->status;
+    }
+    const double* w = p->rho_weights;
+    p->report.primal_res = q[Q_DGP] / (w[0] * w[0]) + q[Q_DGT] / (w[1] * w[1]) + q[Q_DGV] / (w[2] * w[2]) +
+                           q[Q_DGS] / (w[3] * w[3]);
+    p->report.dual_gamma = q[Q_DGP] + q[Q_DGT] + q[Q_DGV] + q[Q_DGS];
+    const mf_params* pr = &p->last_params;
+    p->report.objective = q[Q_FIT] + 0.5 * pr->mu_eps * q[Q_X2] + pr->mu_s * q[Q_L1S] + pr->mu_nu * q[Q_L1NU];
+    p->report.x_min = q[Q_XMIN];
+    p->report.x_norm2 = q[Q_X2];
+    p->report_pending = 0;
+    bool finite = q[Q_NONFIN] == 0.0;
+    for (int i = 0; i < Q_COUNT; i++) finite = finite && std::isfinite(q[i]);
+    if (!finite && p->status == MF_OK) p->status = MF_ERR_NONFINITE;
+  }
+  *r = p->report;
+  return p->status;
+}
+
+mf_status mf_plan_set_timing(mf_plan* p, int enable) {
+  if (!p) return MF_ERR_INVALID;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return MF_ERR_CUDA;
+  p->ev_used = 0;
+  p->ev_kernel.clear();
+  for (int k = 0; k < MF_K_COUNT; k++) {
+    p->kernel_ms[k] = 0.0;
+    p->launches[k] = 0;
+  }
+  p->timing = enable ? 1 : 0;
+  return MF_OK;
+}
+
+mf_status mf_plan_get_timing(mf_plan* p, int kernel, double* total_ms, long long* launches) {
+  if (!p || kernel < 0 || kernel >= MF_K_COUNT) return MF_ERR_INVALID;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return MF_ERR_CUDA;
+  fold_timing(p);
+  if (total_ms) *total_ms = p->kernel_ms[kernel];
+  if (launches) *launches = p->launches[kernel];
+  return MF_OK;
+}
+
+const char* mf_kernel_name(int kernel) {
+  static const char* names[MF_K_COUNT] = {"rows_fwd", "cols_solve", "rows_inv", "spectral", "wav_ll",
+                                          "wav_level1", "wav_levelj", "setup", "reduce"};
+  return (kernel >= 0 && kernel < MF_K_COUNT) ? names[kernel] : "unknown";
+}
+
+mf_status mf_wavelet_filter(int K, double* taps, int* len) {
+  if (K < 1 || K > MF_MAX_K) return MF_ERR_INVALID;
+  if (len) *len = 2 * K;
+  if (taps) std::memcpy(taps, filter_taps(K), sizeof(double) * 2 * K);
+  return MF_OK;
+}
+
+const char* mf_status_string(mf_status s) {
+  switch (s) {
+    case MF_OK: return "ok";
+    case MF_ERR_INVALID: return "invalid argument";
+    case MF_ERR_OOM: return "device out of memory";
+    case MF_ERR_CUDA: return "CUDA error";
+    case MF_ERR_TIMEOUT: return "device wait timed out";
+    case MF_ERR_NONFINITE: return "non-finite value in the iterate";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

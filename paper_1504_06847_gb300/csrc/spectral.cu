@@ -1,0 +1,291 @@
+// Steps II, IV, V and the matching duals of step VI (Algorithm 1), one pixel
+// spectrum (the L values of a row of X) at a time, and the pointwise part of
+// the next right-hand side (Eq. matB):
+//   P~ = X - Gamma_P / rho_P,  P = max(0, P~),  Gamma_P += rho_P (P - X)      (II, VI)
+//   V  = S_{mu_nu/rho_V}(S W_nu - Gamma_V / rho_V)              old S        (IV)
+//   S  = ((Gamma_V + rho_V V) W_nu^T - Gamma_S + rho_S X) / (rho_V + rho_S)  (V, m_nu = 1)
+//   Gamma_V += rho_V (V - S W_nu),  Gamma_S += rho_S (S - X)       new S     (VI)
+//   b = Gamma_P + rho_P P + Gamma_S + rho_S S
+// W_nu is the orthonormal DCT-II (Section 4), so S and Gamma_S are kept in the
+// DCT domain (S W_nu, Gamma_S W_nu): step V becomes pointwise there and an
+// iteration needs two length-L DCTs per pixel (X W_nu forward, and
+// (Gamma_S + rho_S S) back), each a (pixels x L) . (L x L) contraction done here
+// as a register-tiled FP32 product out of shared memory.
+#include <cuda_runtime.h>
+
+#include "mf_internal.cuh"
+#include "reduce.cuh"
+
+namespace mf {
+
+constexpr int SP_NT = 256;
+
+template <class R> struct V4;
+template <> struct V4<float> {
+  static __device__ __forceinline__ void ld(const float* p, float* v) {
+    float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+  static __device__ __forceinline__ void st(float* p, const float* v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <> struct V4<double> {
+  static __device__ __forceinline__ void ld(const double* p, double* v) {
+    double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+  static __device__ __forceinline__ void st(double* p, const double* v) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+
+template <class R> __device__ __forceinline__ R soft_thr(R t, R tau) {
+  const R a = fabs(t) - tau;
+  return a > (R)0 ? copysign(a, t) : (R)0;
+}
+
+template <class R> __device__ __forceinline__ bool finite_(R v) { return isfinite(v); }
+
+template <class R, int LP, int RESID>
+__global__ void __launch_bounds__(SP_NT) k_spectral(const R* __restrict__ X, R* __restrict__ GP, R* __restrict__ Sd,
+                                                     R* __restrict__ GV, R* __restrict__ GSd, R* __restrict__ b,
+                                                     const R* __restrict__ dctC, int NN, int L, IterScalars<R> sc,
+                                                     double* __restrict__ partials) {
+  constexpr int PT = 4096 / LP;   // pixels per CTA
+  constexpr int TP = PT / 4;      // thread columns (4 pixels each)
+  static_assert((LP / 4) * TP == SP_NT, "tile");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* C = reinterpret_cast<R*>(smem_raw);   // C[k][l]
+  R* CT = C + LP * LP;                      // CT[l][k]
+  R* T = CT + LP * LP;                      // tile [LP][PT]: X, then U
+  const int tid = threadIdx.x;
+  const int tk = tid / TP, tp = tid % TP;
+  const int p0 = blockIdx.x * PT;
+
+  for (int e = tid; e < LP * LP; e += SP_NT) {
+    const int k = e / LP, l = e % LP;
+    const R v = (k < L && l < L) ? dctC[k * L + l] : (R)0;
+    C[k * LP + l] = v;
+    CT[l * LP + k] = v;
+  }
+  for (int e = tid; e < LP * (PT / 4); e += SP_NT) {
+    const int l = e / (PT / 4), p = 4 * (e % (PT / 4));
+    R v[4] = {0, 0, 0, 0};
+    if (l < L && p0 + p < NN) V4<R>::ld(X + (size_t)l * NN + p0 + p, v);
+    V4<R>::st(T + l * PT + p, v);
+  }
+  __syncthreads();
+
+  const int kb = 4 * tk, pb = 4 * tp;
+  const bool pix_ok = p0 + pb < NN;
+  R xr[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; a++) V4<R>::ld(T + (kb + a) * PT + pb, xr[a]);
+
+  // x^[k][p] = sum_l C[k][l] X[l][p]
+  R acc[4][4] = {};
+#pragma unroll 4
+  for (int l = 0; l < LP; l++) {
+    R c4[4], x4[4];
+    V4<R>::ld(CT + l * LP + kb, c4);
+    V4<R>::ld(T + l * PT + pb, x4);
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int c = 0; c < 4; c++) acc[a][c] = fma(c4[a], x4[c], acc[a][c]);
+  }
+
+  double q[Q_COUNT];
+  if (RESID) {
+#pragma unroll
+    for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
+    q[Q_XMIN] = 1e300;
+  }
+
+  // DCT-domain part of steps IV, V and VI
+  R u[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    const int k = kb + a;
+    if (k < L && pix_ok) {
+      const size_t o = (size_t)k * NN + p0 + pb;
+      R s[4], gv[4], gs[4];
+      V4<R>::ld(Sd + o, s);
+      V4<R>::ld(GV + o, gv);
+      V4<R>::ld(GSd + o, gs);
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        const R xh = acc[a][c];
+        const R v = soft_thr<R>(s[c] - gv[c] * sc.inv_rho_V, sc.tau_V);
+        const R sn = (gv[c] + sc.rho_V * v - gs[c] + sc.rho_S * xh) * sc.inv_VS;
+        const R gvn = gv[c] + sc.rho_V * (v - sn);
+        const R gsn = gs[c] + sc.rho_S * (sn - xh);
+        if (RESID) {
+          const double dv = (double)gvn - (double)gv[c], ds = (double)gsn - (double)gs[c];
+          q[Q_DGV] += dv * dv;
+          q[Q_DGS] += ds * ds;
+          q[Q_L1NU] += fabs((double)xh);
+          if (!finite_<R>(gvn) || !finite_<R>(gsn)) q[Q_NONFIN] += 1.0;
+        }
+        s[c] = sn;
+        gv[c] = gvn;
+        gs[c] = gsn;
+        u[a][c] = gsn + sc.rho_S * sn;
+      }
+      V4<R>::st(Sd + o, s);
+      V4<R>::st(GV + o, gv);
+      V4<R>::st(GSd + o, gs);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; c++) u[a][c] = (R)0;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 4; a++) V4<R>::st(T + (kb + a) * PT + pb, u[a]);
+  __syncthreads();
+
+  // (Gamma_S + rho_S S)[l][p] = sum_k C[k][l] U[k][p]
+  R bs[4][4] = {};
+#pragma unroll 4
+  for (int k = 0; k < LP; k++) {
+    R c4[4], u4[4];
+    V4<R>::ld(C + k * LP + kb, c4);
+    V4<R>::ld(T + k * PT + pb, u4);
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int c = 0; c < 4; c++) bs[a][c] = fma(c4[a], u4[c], bs[a][c]);
+  }
+
+  // pixel-domain part: step II, Gamma_P, and b
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    const int l = kb + a;
+    if (l < L && pix_ok) {
+      const size_t o = (size_t)l * NN + p0 + pb;
+      R gp[4], bo[4];
+      V4<R>::ld(GP + o, gp);
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        const R x = xr[a][c];
+        const R pt = x - gp[c] * sc.inv_rho_P;
+        const R pp = pt > (R)0 ? pt : (R)0;
+        const R gpn = gp[c] + sc.rho_P * (pp - x);
+        if (RESID) {
+          const double d = (double)gpn - (double)gp[c];
+          q[Q_DGP] += d * d;
+          q[Q_X2] += (double)x * (double)x;
+          q[Q_XMIN] = fmin(q[Q_XMIN], (double)x);
+          if (!finite_<R>(x) || !finite_<R>(gpn)) q[Q_NONFIN] += 1.0;
+        }
+        gp[c] = gpn;
+        bo[c] = gpn + sc.rho_P * pp + bs[a][c];
+      }
+      V4<R>::st(GP + o, gp);
+      V4<R>::st(b + o, bo);
+    }
+  }
+  if (RESID) block_reduce_write<SP_NT>(q, partials + (size_t)blockIdx.x * MF_NQ);
+}
+
+template <class R, int LP>
+static cudaError_t spectral_lp(const R* X, R* GP, R* Sd, R* GV, R* GSd, R* b, const R* dctC, int N, int L,
+                               IterScalars<R> sc, double* partials, int resid, cudaStream_t s) {
+  constexpr int PT = 4096 / LP;
+  const int NN = N * N;
+  const int blocks = (NN + PT - 1) / PT;
+  const size_t sm = sizeof(R) * (2 * LP * LP + LP * PT);
+  cudaError_t e;
+  if (resid) {
+    e = cudaFuncSetAttribute(k_spectral<R, LP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_spectral<R, LP, 1><<<blocks, SP_NT, sm, s>>>(X, GP, Sd, GV, GSd, b, dctC, NN, L, sc, partials);
+  } else {
+    e = cudaFuncSetAttribute(k_spectral<R, LP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_spectral<R, LP, 0><<<blocks, SP_NT, sm, s>>>(X, GP, Sd, GV, GSd, b, dctC, NN, L, sc, partials);
+  }
+  return cudaGetLastError();
+}
+
+static int padded_L(int L) {
+  int lp = 8;
+  while (lp < L) lp *= 2;
+  return lp;
+}
+
+template <class R>
+int spectral_blocks(int N, int L) {
+  const int PT = 4096 / padded_L(L);
+  return (N * N + PT - 1) / PT;
+}
+
+template <class R>
+cudaError_t launch_spectral(const R* X, R* GP, R* Sd, R* GV, R* GSd, R* b, const R* dctC, int N, int L,
+                            IterScalars<R> sc, double* partials, int resid, cudaStream_t s) {
+  switch (padded_L(L)) {
+    case 8: return spectral_lp<R, 8>(X, GP, Sd, GV, GSd, b, dctC, N, L, sc, partials, resid, s);
+    case 16: return spectral_lp<R, 16>(X, GP, Sd, GV, GSd, b, dctC, N, L, sc, partials, resid, s);
+    case 32: return spectral_lp<R, 32>(X, GP, Sd, GV, GSd, b, dctC, N, L, sc, partials, resid, s);
+    case 64: return spectral_lp<R, 64>(X, GP, Sd, GV, GSd, b, dctC, N, L, sc, partials, resid, s);
+    case 128:
+      if (sizeof(R) == 8) return cudaErrorInvalidValue;
+      return spectral_lp<R, 128>(X, GP, Sd, GV, GSd, b, dctC, N, L, sc, partials, resid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_spectral<float>(const float*, float*, float*, float*, float*, float*, const float*, int,
+                                            int, IterScalars<float>, double*, int, cudaStream_t);
+template cudaError_t launch_spectral<double>(const double*, double*, double*, double*, double*, double*,
+                                             const double*, int, int, IterScalars<double>, double*, int,
+                                             cudaStream_t);
+template int spectral_blocks<float>(int, int);
+template int spectral_blocks<double>(int, int);
+
+// FP64 fold of the per-block partials into sums[MF_NQ]: a fixed thread count
+// and a fixed tree order, so the result does not depend on scheduling.
+constexpr int FIN_NT = 512;
+__global__ void __launch_bounds__(FIN_NT) k_finalize(const double* __restrict__ partials, int nblocks,
+                                                      double* __restrict__ sums, int accumulate) {
+  __shared__ double red[Q_COUNT][FIN_NT];
+  double v[Q_COUNT];
+#pragma unroll
+  for (int q = 0; q < Q_COUNT; q++) v[q] = (q == Q_XMIN) ? 1e300 : 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += FIN_NT) {
+#pragma unroll
+    for (int q = 0; q < Q_COUNT; q++) {
+      const double x = partials[(size_t)i * MF_NQ + q];
+      v[q] = (q == Q_XMIN) ? fmin(v[q], x) : v[q] + x;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < Q_COUNT; q++) red[q][threadIdx.x] = v[q];
+  __syncthreads();
+  for (int w = FIN_NT / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+#pragma unroll
+      for (int q = 0; q < Q_COUNT; q++) {
+        const double a = red[q][threadIdx.x], c = red[q][threadIdx.x + w];
+        red[q][threadIdx.x] = (q == Q_XMIN) ? fmin(a, c) : a + c;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < Q_COUNT) {
+    const int q = threadIdx.x;
+    const double r = red[q][0];
+    if (accumulate) sums[q] = (q == Q_XMIN) ? fmin(sums[q], r) : sums[q] + r;
+    else sums[q] = r;
+  }
+}
+
+cudaError_t launch_finalize(const double* partials, int nblocks, double* sums, int accumulate, cudaStream_t s) {
+  k_finalize<<<1, FIN_NT, 0, s>>>(partials, nblocks, sums, accumulate);
+  return cudaGetLastError();
+}
+
+}  // namespace mf
