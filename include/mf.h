@@ -46,7 +46,8 @@ typedef enum {
   MF_ERR_OOM = 2,       /* device allocation failed */
   MF_ERR_CUDA = 3,      /* a CUDA call or launch failed */
   MF_ERR_TIMEOUT = 4,   /* a bounded device wait expired */
-  MF_ERR_NONFINITE = 5  /* a NaN/Inf was seen by a residual reduction */
+  MF_ERR_NONFINITE = 5, /* a NaN/Inf was seen by a residual reduction */
+  MF_ERR_TOO_LARGE = 6  /* the cube exceeds MF_XSTEP_NOALLOC_MAX_VOXELS */
 } mf_status;
 
 typedef enum {
@@ -162,6 +163,40 @@ const char* mf_kernel_name(int kernel);
 mf_status mf_wavelet_filter(int K, double* taps_host, int* len);
 
 const char* mf_status_string(mf_status s);
+
+/*
+ * Step I without any allocation: x = (H^T H + rho I)^-1 (H^T y + b) per band,
+ * rho = mu_eps + rho_S + rho_P + n_s rho_T with n_s the number of bases in
+ * prm->wavelet_mask -- the same solve, on the same kernels, as the first step
+ * of an mf_admm_iterate iteration whose right-hand side (MF_ARR_B) is b.
+ *
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory at all -- code running where cudaMalloc is
+ * unavailable or forbidden (inside a host callback or another library's
+ * allocator hook, under a caller-owned memory pool or budget, or a real-time
+ * path that must not block on the allocator).  Plans need cudaMalloc; this
+ * call does not.  Its working memory is one file-scope static __device__
+ * array of about 10.4 MB (MF_XSTEP_NOALLOC_MAX_VOXELS = 2^19 voxels:
+ * e.g. 256 x 256 x 8 or 128 x 128 x 32), which every GPU that loads the
+ * library holds until the process exits.  Larger cubes return
+ * MF_ERR_TOO_LARGE before any device work.
+ *
+ *   psf_cube, y_cube, b_cube : device [L][N][N] float inputs (read only)
+ *   x_out                    : device [L][N][N] float output (also used as a
+ *                              temporary during the call)
+ *   prm                      : mu_eps, rho_P, rho_T, rho_S, wavelet_mask and
+ *                              stream are read; other fields are ignored.
+ * The first call on a device looks up the static array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array, which keeps
+ * the last call's contents (each call overwrites everything it reads), so
+ * calls whose work overlaps on the GPU -- on different streams or host
+ * threads -- race; serialise them.  The work is enqueued on prm->stream and
+ * the call returns; errors: MF_ERR_INVALID, MF_ERR_TOO_LARGE, MF_ERR_CUDA.
+ */
+#define MF_XSTEP_NOALLOC_MAX_VOXELS (1u << 19)
+mf_status mf_xstep_noalloc(int N, int L, const float* psf_cube, const float* y_cube, const float* b_cube,
+                           const mf_params* prm, float* x_out);
 
 #ifdef __cplusplus
 }

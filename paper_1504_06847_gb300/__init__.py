@@ -14,7 +14,8 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmf.so")
 
-MF_OK, MF_ERR_INVALID, MF_ERR_OOM, MF_ERR_CUDA, MF_ERR_TIMEOUT, MF_ERR_NONFINITE = range(6)
+MF_OK, MF_ERR_INVALID, MF_ERR_OOM, MF_ERR_CUDA, MF_ERR_TIMEOUT, MF_ERR_NONFINITE, MF_ERR_TOO_LARGE = range(7)
+XSTEP_NOALLOC_MAX_VOXELS = 1 << 19
 MF_FP32, MF_FP64, MF_FP32_DCT_SPLITBF16 = range(3)
 ARR_X, ARR_GAMMA_P, ARR_S_DCT, ARR_GAMMA_V, ARR_GAMMA_S_DCT, ARR_B, ARR_GAMMA_T = range(7)
 
@@ -22,7 +23,7 @@ EXPORTS = ["mf_params_default", "mf_plan_create", "mf_plan_create_f64", "mf_plan
            "mf_plan_device_bytes", "mf_admm_iterate", "mf_admm_iterate_f64", "mf_plan_get_array",
            "mf_plan_set_array", "mf_plan_get_state", "mf_plan_set_state", "mf_plan_get_report",
            "mf_wavelet_filter", "mf_status_string", "mf_plan_set_timing", "mf_plan_get_timing",
-           "mf_kernel_name"]
+           "mf_kernel_name", "mf_xstep_noalloc"]
 
 KERNELS = ["rows_fwd", "cols_solve", "rows_inv", "spectral", "wav_ll", "wav_level1", "wav_levelj", "setup",
            "reduce"]
@@ -99,6 +100,8 @@ def lib():
         L.mf_plan_get_timing.restype = ctypes.c_int
         L.mf_kernel_name.argtypes = [ctypes.c_int]
         L.mf_kernel_name.restype = ctypes.c_char_p
+        L.mf_xstep_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.POINTER(Params), vp]
+        L.mf_xstep_noalloc.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -128,6 +131,26 @@ def wavelet_filter(K: int):
     n = ctypes.c_int()
     _check(lib().mf_wavelet_filter(K, taps, ctypes.byref(n)), "mf_wavelet_filter")
     return [taps[i] for i in range(n.value)]
+
+
+def xstep_noalloc(psf, y, b, x_out, **kw):
+    """Step I, x = (H^T H + rho I)^-1 (H^T y + b), without any device allocation
+    (the library's static scratch; see mf_xstep_noalloc in include/mf.h).  For
+    callers that cannot allocate device memory: all arguments are existing
+    float32 CUDA tensors [L, N, N]; x_out receives the result.  Enqueued on the
+    current stream unless ``stream`` is given."""
+    import torch
+
+    L_, N_ = int(y.shape[0]), int(y.shape[-1])
+    for t in (psf, y, b, x_out):
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != (L_, N_, N_):
+            raise ValueError("psf, y, b, x_out must be contiguous float32 CUDA tensors [L, N, N]")
+    if "stream" not in kw:
+        kw["stream"] = torch.cuda.current_stream(y.device).cuda_stream
+    p = default_params(**kw)
+    _check(lib().mf_xstep_noalloc(N_, L_, ctypes.c_void_p(psf.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                  ctypes.c_void_p(b.data_ptr()), ctypes.byref(p), ctypes.c_void_p(x_out.data_ptr())),
+           "mf_xstep_noalloc")
 
 
 class Plan:

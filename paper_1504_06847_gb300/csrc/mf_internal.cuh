@@ -151,6 +151,9 @@ template <class R> cudaError_t launch_wav_level(const R* in, size_t in_band_stri
                                                 cudaStream_t s);
 template <class R> int wav_level_blocks(int M, int L, int nd);
 
+// ifftshift of a PSF cube (peak from (N/2, N/2) to (0, 0)).
+template <class R> cudaError_t launch_shift_psf(const R* psf, R* out, int N, size_t total, cudaStream_t s);
+
 cudaError_t launch_finalize(const double* partials, int nblocks, double* sums, int accumulate, cudaStream_t s);
 
 }  // namespace mf

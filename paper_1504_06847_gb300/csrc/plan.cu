@@ -414,6 +414,15 @@ void* array_ptr(mf_plan* p, int which, size_t* count) {
 
 }  // namespace
 
+namespace mf {
+template <class R>
+cudaError_t launch_shift_psf(const R* psf, R* out, int N, size_t total, cudaStream_t s) {
+  k_shift_psf<R><<<1024, 256, 0, s>>>(psf, out, N, total);
+  return cudaGetLastError();
+}
+template cudaError_t launch_shift_psf<float>(const float*, float*, int, size_t, cudaStream_t);
+}  // namespace mf
+
 extern "C" {
 
 void mf_params_default(mf_params* p) {
@@ -585,6 +594,7 @@ const char* mf_status_string(mf_status s) {
     case MF_ERR_CUDA: return "CUDA error";
     case MF_ERR_TIMEOUT: return "device wait timed out";
     case MF_ERR_NONFINITE: return "non-finite value in the iterate";
+    case MF_ERR_TOO_LARGE: return "cube exceeds the static scratch of the no-allocation entry point";
     default: return "unknown status";
   }
 }
