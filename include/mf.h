@@ -158,6 +158,15 @@ mf_status mf_plan_set_timing(mf_plan* p, int enable);
 mf_status mf_plan_get_timing(mf_plan* p, int kernel, double* total_ms, long long* launches);
 const char* mf_kernel_name(int kernel);
 
+/* Performance options of a plan.  They change launch shapes only: every option
+ * value computes the same arithmetic per element in the same order, so
+ * results are bitwise identical.
+ *   MF_OPT_WAV_TILE: output tile edge of the fused wavelet level kernels,
+ *                    64 (default) or 32; levels smaller than the tile use
+ *                    the largest tile that fits. */
+typedef enum { MF_OPT_WAV_TILE = 0 } mf_option;
+mf_status mf_plan_set_option(mf_plan* p, int option, int value);
+
 /* Host copy of the library's low-pass filter DbK (K = 1..8, 2K taps, double),
  * built at load time from Daubechies' spectral factorisation. */
 mf_status mf_wavelet_filter(int K, double* taps_host, int* len);

@@ -23,7 +23,8 @@ EXPORTS = ["mf_params_default", "mf_plan_create", "mf_plan_create_f64", "mf_plan
            "mf_plan_device_bytes", "mf_admm_iterate", "mf_admm_iterate_f64", "mf_plan_get_array",
            "mf_plan_set_array", "mf_plan_get_state", "mf_plan_set_state", "mf_plan_get_report",
            "mf_wavelet_filter", "mf_status_string", "mf_plan_set_timing", "mf_plan_get_timing",
-           "mf_kernel_name", "mf_xstep_noalloc"]
+           "mf_kernel_name", "mf_xstep_noalloc", "mf_plan_set_option"]
+MF_OPT_WAV_TILE = 0
 
 KERNELS = ["rows_fwd", "cols_solve", "rows_inv", "spectral", "wav_ll", "wav_level1", "wav_levelj", "setup",
            "reduce"]
@@ -100,6 +101,8 @@ def lib():
         L.mf_plan_get_timing.restype = ctypes.c_int
         L.mf_kernel_name.argtypes = [ctypes.c_int]
         L.mf_kernel_name.restype = ctypes.c_char_p
+        L.mf_plan_set_option.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+        L.mf_plan_set_option.restype = ctypes.c_int
         L.mf_xstep_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.POINTER(Params), vp]
         L.mf_xstep_noalloc.restype = ctypes.c_int
         _lib = L
@@ -238,6 +241,10 @@ class Plan:
         d = r.as_dict()
         d["status"] = rc
         return d
+
+    def set_option(self, option: int, value: int):
+        """Launch-shape option (results are bitwise identical for every value)."""
+        _check(lib().mf_plan_set_option(self._h, option, value), "mf_plan_set_option")
 
     def set_timing(self, enable: bool):
         """Per-kernel CUDA-event timing on the plan's stream (resets the counters)."""

@@ -101,6 +101,7 @@ struct mf_plan {
   int report_pending;   // sums on the device not yet folded into report
   double rho_weights[4];
   mf_params last_params;
+  int wav_tile;         // preferred wavelet tile edge (MF_OPT_WAV_TILE)
   // per-kernel timing
   int timing;
   long long launches[MF_K_COUNT];
@@ -144,12 +145,16 @@ template <class R> cudaError_t launch_wav_ll(const R* in, size_t in_band_stride,
                                              R* out, int M, int L, int nd, const WavSet<R>* ws, cudaStream_t s);
 // Fused level: analysis of the M x M input, thresholds and dual update of the level's
 // coefficients, synthesis into the M x M output (or accumulation into b at level 1).
+// pref_tile: preferred output tile edge (64 or 32) where the level is large enough.
 template <class R> cudaError_t launch_wav_level(const R* in, size_t in_band_stride, size_t in_basis_stride,
                                                 const R* rcoarse, R* out, const R* gt_old, R* gt_new,
                                                 int N, int M, int L, int coarsest, int nd, const WavSet<R>* ws,
-                                                IterScalars<R> sc, double* partials, int resid,
+                                                IterScalars<R> sc, double* partials, int resid, int pref_tile,
                                                 cudaStream_t s);
-template <class R> int wav_level_blocks(int M, int L, int nd);
+template <class R> int wav_level_blocks(int M, int L, int nd, int pref_tile);
+// Copies the Daubechies tap tables into the wavelet kernels' constant memory
+// (current device; the values are the same for every plan).
+cudaError_t upload_taps();
 
 // ifftshift of a PSF cube (peak from (N/2, N/2) to (0, 0)).
 template <class R> cudaError_t launch_shift_psf(const R* psf, R* out, int N, size_t total, cudaStream_t s);

@@ -120,6 +120,7 @@ mf_status create(int N, int L, const R* psf, mf_plan** out) {
   p->esz = sizeof(R);
   p->cube = (size_t)N * N * L;
   p->report.resid_iter = -1;
+  p->wav_tile = 64;
   const size_t cb = p->cube * sizeof(R);
   const size_t half = (size_t)L * N * (N / 2) * sizeof(cx<R>);
   const size_t nyq = (size_t)L * N * sizeof(cx<R>);
@@ -148,8 +149,10 @@ mf_status create(int N, int L, const R* psf, mf_plan** out) {
   // partial rows: the largest grid of any kernel that reduces
   size_t cap = (size_t)spectral_blocks<R>(N, L);
   for (int M = N; M >= 4; M /= 2) {
-    const size_t nb = (size_t)wav_level_blocks<R>(M, L, M == N ? 1 : MF_MAX_BASES);
-    if (nb > cap) cap = nb;
+    for (int pref = 32; pref <= 64; pref *= 2) {
+      const size_t nb = (size_t)wav_level_blocks<R>(M, L, M == N ? 1 : MF_MAX_BASES, pref);
+      if (nb > cap) cap = nb;
+    }
   }
   const size_t colblocks = (size_t)L * N;  // upper bound of the column kernel's grid
   if (colblocks > cap) cap = colblocks;
@@ -177,9 +180,10 @@ mf_status create(int N, int L, const R* psf, mf_plan** out) {
     }
     cudaError_t e1 = cudaMemcpy(p->tw, tw, sizeof(cx<R>) * N, cudaMemcpyHostToDevice);
     cudaError_t e2 = cudaMemcpy(p->dctC, C, sizeof(R) * L * L, cudaMemcpyHostToDevice);
+    cudaError_t e3 = upload_taps();
     delete[] tw;
     delete[] C;
-    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
       free_plan_memory(p);
       delete p;
       return MF_ERR_CUDA;
@@ -315,12 +319,13 @@ cudaError_t iteration(mf_plan* p, int J, int nd, const WavSet<R>* wsd, const Ite
     {
       Timed t(p, j == 1 ? MF_K_WAV_LEVEL1 : MF_K_WAV_LEVELJ, s);
       if ((e = launch_wav_level<R>(in, 0, 0, rco, outp, gto, gtn, N, M, L, j == J, nd, wsd, sc, p->partials,
-                                   resid, s)))
+                                   resid, p->wav_tile, s)))
         return e;
     }
     if (resid) {
       Timed t(p, MF_K_REDUCE, s);
-      if ((e = launch_finalize(p->partials, wav_level_blocks<R>(M, L, M == N ? 1 : nd), p->sums, 1, s))) return e;
+      if ((e = launch_finalize(p->partials, wav_level_blocks<R>(M, L, M == N ? 1 : nd, p->wav_tile), p->sums, 1, s)))
+        return e;
     }
   }
   p->gt_cur = 1 - p->gt_cur;
@@ -571,6 +576,18 @@ mf_status mf_plan_get_timing(mf_plan* p, int kernel, double* total_ms, long long
   if (total_ms) *total_ms = p->kernel_ms[kernel];
   if (launches) *launches = p->launches[kernel];
   return MF_OK;
+}
+
+mf_status mf_plan_set_option(mf_plan* p, int option, int value) {
+  if (!p) return MF_ERR_INVALID;
+  switch (option) {
+    case MF_OPT_WAV_TILE:
+      if (value != 32 && value != 64) return MF_ERR_INVALID;
+      if (cudaStreamSynchronize(p->stream) != cudaSuccess) return MF_ERR_CUDA;
+      p->wav_tile = value;
+      return MF_OK;
+    default: return MF_ERR_INVALID;
+  }
 }
 
 const char* mf_kernel_name(int kernel) {

@@ -34,6 +34,44 @@ constexpr int OPT = WT * WT / WNT;           // output pixels per thread
 constexpr int LT = 32;                       // output tile edge of the low-low kernel
 constexpr int LIM = 2 * LT + 2 * MF_MAX_K - 2;
 
+// Daubechies taps by half-length K (the same numbers for every plan):
+// low-pass h_n and high-pass g_n = (-1)^n h_{2K-1-n}.  With K and n known at
+// compile time the FMAs read them straight from the constant bank.
+__constant__ float c_hf[MF_MAX_K + 1][MF_MAX_F];
+__constant__ float c_gf[MF_MAX_K + 1][MF_MAX_F];
+__constant__ double c_hd[MF_MAX_K + 1][MF_MAX_F];
+__constant__ double c_gd[MF_MAX_K + 1][MF_MAX_F];
+
+template <class R> struct Taps;
+template <> struct Taps<float> {
+  static __device__ __forceinline__ float h(int K, int n) { return c_hf[K][n]; }
+  static __device__ __forceinline__ float g(int K, int n) { return c_gf[K][n]; }
+};
+template <> struct Taps<double> {
+  static __device__ __forceinline__ double h(int K, int n) { return c_hd[K][n]; }
+  static __device__ __forceinline__ double g(int K, int n) { return c_gd[K][n]; }
+};
+
+cudaError_t upload_taps() {
+  float hf[MF_MAX_K + 1][MF_MAX_F] = {}, gf[MF_MAX_K + 1][MF_MAX_F] = {};
+  double hd[MF_MAX_K + 1][MF_MAX_F] = {}, gd[MF_MAX_K + 1][MF_MAX_F] = {};
+  for (int K = 1; K <= MF_MAX_K; K++) {
+    const double* h = filter_taps(K);
+    for (int n = 0; n < 2 * K; n++) {
+      const double gv = (n & 1) ? -h[2 * K - 1 - n] : h[2 * K - 1 - n];
+      hd[K][n] = h[n];
+      gd[K][n] = gv;
+      hf[K][n] = (float)h[n];
+      gf[K][n] = (float)gv;
+    }
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_hf, hf, sizeof(hf));
+  if (!e) e = cudaMemcpyToSymbol(c_gf, gf, sizeof(gf));
+  if (!e) e = cudaMemcpyToSymbol(c_hd, hd, sizeof(hd));
+  if (!e) e = cudaMemcpyToSymbol(c_gd, gd, sizeof(gd));
+  return e;
+}
+
 template <class R> __device__ __forceinline__ R soft_w(R t, R tau) {
   const R a = fabs(t) - tau;
   return a > (R)0 ? copysign(a, t) : (R)0;
@@ -280,6 +318,401 @@ __global__ void __launch_bounds__(WNT) k_wav_levelj(const R* __restrict__ in_img
         q, partials + (((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * MF_NQ);
 }
 
+// ---------------------------------------------------------------------------
+// T x T output tiles (T = 64 or 32, M >= T): compile-time shapes, runs of RB
+// outputs per thread along the filter direction, odd shared-memory pitches so
+// that consecutive rows fall in different banks.
+// ---------------------------------------------------------------------------
+template <int T>
+struct TC {
+  static constexpr int RB = 4;                                  // outputs per run
+  static constexpr int IR = T + 4 * MF_MAX_K - 4;               // input rows / columns (halo for K = 8)
+  static constexpr int CWM = T / 2 + MF_MAX_K - 1;              // largest coefficient tile edge
+  static constexpr int NRM = (CWM + RB - 1) / RB;               // runs per coefficient line
+  static constexpr int NVM = 2 * RB - 2 + 2 * MF_MAX_K;         // inputs of one analysis run
+  static constexpr int RD = 2 * RB * (NRM - 1) + NVM;           // extent read by the analysis runs
+  static constexpr int IP = (RD > IR ? RD : IR) | 1;            // input pitch
+  static constexpr int CR = RD > IR ? RD : IR;                  // rows of the row-analysis buffers
+  static constexpr int CP = (RB * NRM) | 1;                     // coefficient pitch
+  static constexpr int SR = RB * NRM;                           // rows of each sub-band buffer
+  static constexpr int SBQ = SR * CP;                           // stride between sub-band buffers
+  static constexpr int SMEM = IR * IP + 2 * CR * CP + 4 * SBQ;  // elements
+  static constexpr int BP = T + 1;                              // pitch of the level-1 b accumulator
+  static constexpr int SMEM1 = SMEM + T * BP;
+  static constexpr int OPI = (T * T / WNT) < 8 ? (T * T / WNT) : 8;  // outputs of one synthesis item
+  static constexpr int IPT = T * T / (WNT * OPI);                    // synthesis items per thread
+  static constexpr int MINB = T == 64 ? 2 : 4;                       // CTAs per SM
+};
+
+template <class R, int T>
+__device__ __forceinline__ R* tile_smem(R*& ra, R*& rd, R*& sb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* in = reinterpret_cast<R*>(smem_raw);
+  ra = in + TC<T>::IR * TC<T>::IP;
+  rd = ra + TC<T>::CR * TC<T>::CP;
+  sb = rd + TC<T>::CR * TC<T>::CP;
+  return in;
+}
+
+// One basis (half-length K) on one T x T output tile.  in: input tile with
+// pitch TC<T>::IP, loaded for half-length Kin >= K at offset off = 2 (Kin - K).
+// emit(s, m, x, v[OPI]) receives output row m, columns x..x+OPI-1 for the
+// thread's item s (fixed across calls).
+template <class R, int T, int K, int RESID, class Emit>
+__device__ __forceinline__ void level_tile_t(const R* in, int off, R* ra, R* rd, R* sb, const R* __restrict__ h,
+                                             const R* __restrict__ g, int M, int y0, int x0,
+                                             const R* __restrict__ gto, R* __restrict__ gtn, int N,
+                                             const R* __restrict__ rco, const IterScalars<R>& sc, R w, double* q,
+                                             Emit emit) {
+  typedef TC<T> C;
+  constexpr int F = 2 * K;
+  constexpr int CW = T / 2 + K - 1;     // coefficients per tile edge (with the synthesis halo)
+  constexpr int IH = T + 4 * K - 4;     // input rows used
+  constexpr int RB = C::RB;             // outputs per thread run
+  constexpr int B_IP = C::IP, B_CP = C::CP, SBQ = C::SBQ, OPI = C::OPI;
+  constexpr int NRUN = (CW + RB - 1) / RB;
+  constexpr int NV = 2 * RB - 2 + F;    // inputs of a run of RB analysis outputs
+  constexpr int NU = RB / 2 + K - 1;    // coefficients of a run of RB synthesis outputs
+  const int tid = threadIdx.x;
+#define hr(n) Taps<R>::h(K, n)
+#define gr(n) Taps<R>::g(K, n)
+  // 1. row analysis: row r, coefficients RB j..RB j+RB-1 (low into ra, high into rd);
+  //    consecutive threads take consecutive rows
+  for (int it = tid; it < IH * NRUN; it += WNT) {
+    const int r = it % IH, j = it / IH;
+    const R* src = in + (off + r) * B_IP + off + 2 * RB * j;
+    R v[NV];
+#pragma unroll
+    for (int t = 0; t < NV; t++) v[t] = src[t];
+    R* da = ra + r * B_CP + RB * j;
+    R* dd = rd + r * B_CP + RB * j;
+#pragma unroll
+    for (int c = 0; c < RB; c++) {
+      R a = 0, d = 0;
+#pragma unroll
+      for (int n = 0; n < F; n++) {
+        a = fma(hr(n), v[2 * c + n], a);
+        d = fma(gr(n), v[2 * c + n], d);
+      }
+      da[c] = a;
+      dd[c] = d;
+    }
+  }
+  __syncthreads();
+  // 2. column analysis: column c of ra (sel 0) or rd (sel 1), coefficient rows RB j..
+  for (int it = tid; it < 2 * CW * NRUN; it += WNT) {
+    const int c = it % CW, rest = it / CW;
+    const int j = rest % NRUN, sel = rest / NRUN;
+    const R* col = (sel ? rd : ra) + 2 * RB * j * B_CP + c;
+    R v[NV];
+#pragma unroll
+    for (int t = 0; t < NV; t++) v[t] = col[t * B_CP];
+    R* dlo = sb + (sel ? 1 : 0) * SBQ + RB * j * B_CP + c;  // top-left / top-right
+    R* dhi = sb + (sel ? 3 : 2) * SBQ + RB * j * B_CP + c;  // bottom-left / bottom-right
+#pragma unroll
+    for (int i = 0; i < RB; i++) {
+      R lo = 0, hi = 0;
+#pragma unroll
+      for (int n = 0; n < F; n++) {
+        lo = fma(hr(n), v[2 * i + n], lo);
+        hi = fma(gr(n), v[2 * i + n], hi);
+      }
+      dlo[i * B_CP] = lo;
+      dhi[i * B_CP] = hi;
+    }
+  }
+  __syncthreads();
+  // 3. threshold and dual update of this level's coefficients.  Offsets are
+  //    32-bit within the band image; each thread issues its global loads
+  //    (old Gamma_T, or the coarse reconstruction for the low-low band)
+  //    before using them.
+  {
+    const int Mh = M / 2;
+    const int ci0 = y0 / 2 - (K - 1), cj0 = x0 / 2 - (K - 1);
+    // one coefficient: z in the cell, old Gamma_T (or coarse value) in gam
+    auto update = [&](R* cell, R gam, int gpos, bool own) {
+      if (gpos < 0) {
+        *cell = gam;
+        return;
+      }
+      const R z = *cell;
+      const R tp = soft_w<R>(z - gam * sc.inv_rho_T, sc.tau_T);
+      const R gn = gam + sc.rho_T * (tp - z);
+      *cell = gn + sc.rho_T * tp;
+      if (own) {
+        gtn[gpos] = gn;
+        if (RESID) {
+          const double dg = (double)gn - (double)gam;
+          q[Q_DGT] += (double)w * dg * dg;
+          q[Q_L1S] += (double)w * fabs((double)z);
+          if (!isfinite(gn)) q[Q_NONFIN] += 1.0;
+        }
+      }
+    };
+    // global offset of coefficient (row, col) of the 4 x CW x CW tile (-1: coarse band)
+    auto locate = [&](int row, int c, int& gpos, R& v) {
+      const int qd = row / CW, i = row - (row / CW) * CW;
+      const int gi = (ci0 + i) & (Mh - 1), gc = (cj0 + c) & (Mh - 1);
+      if (qd == 0 && rco != nullptr) {
+        gpos = -1;
+        v = rco[gi * Mh + gc];
+      } else {
+        gpos = (gi + (qd >> 1) * Mh) * N + gc + (qd & 1) * Mh;
+        v = gto[gpos];
+      }
+    };
+    auto owned = [&](int row, int c) {
+      const int i = row - (row / CW) * CW;
+      return (unsigned)(i - (K - 1)) < (unsigned)(T / 2) && (unsigned)(c - (K - 1)) < (unsigned)(T / 2);
+    };
+    if constexpr (CW >= 32 && CW - 32 <= 8) {
+      // groups of 4 rows per warp pass: the 32-wide heads of the 4 rows, then
+      // their tails (columns 32..CW-1) packed 8 lanes per row into one slot
+      const int lane = tid & 31, warp = tid >> 5;
+      constexpr int NG = CW;  // 4 CW rows / 4
+      for (int gidx = warp; gidx < NG; gidx += WNT / 32) {
+        const int r0 = 4 * gidx;
+        R v[5];
+        int gp[5];
+#pragma unroll
+        for (int u = 0; u < 4; u++) locate(r0 + u, lane, gp[u], v[u]);
+        const int trow = r0 + (lane >> 3), tcol = 32 + (lane & 7);
+        const bool tail = tcol < CW;
+        if (tail) locate(trow, tcol, gp[4], v[4]);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const int row = r0 + u;
+          update(sb + (row / CW) * SBQ + (row - (row / CW) * CW) * B_CP + lane, v[u], gp[u], owned(row, lane));
+        }
+        if (tail)
+          update(sb + (trow / CW) * SBQ + (trow - (trow / CW) * CW) * B_CP + tcol, v[4], gp[4], owned(trow, tcol));
+      }
+    } else {
+      // flattened over the tile, TB loads in flight per thread
+      constexpr int NQ = 4 * CW * CW;
+      constexpr int TB = 6;
+      for (int base = 0; base < NQ; base += TB * WNT) {
+        R gv[TB];
+        int gpos[TB];
+#pragma unroll
+        for (int u = 0; u < TB; u++) {
+          const int it = base + tid + u * WNT;
+          if (it < NQ) locate(it / CW, it % CW, gpos[u], gv[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < TB; u++) {
+          const int it = base + tid + u * WNT;
+          if (it < NQ) {
+            const int row = it / CW, c = it % CW;
+            update(sb + (row / CW) * SBQ + (row - (row / CW) * CW) * B_CP + c, gv[u], gpos[u], owned(row, c));
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // 4. column synthesis: output rows RB j.. of coefficient column c; low part
+  //    (from the two left sub-bands) into ra, high part (right sub-bands) into rd
+  for (int it = tid; it < 2 * CW * (T / RB); it += WNT) {
+    const int c = it % CW, rest = it / CW;
+    const int j = rest % (T / RB), sel = rest / (T / RB);
+    const R* Ua = sb + (sel ? 1 : 0) * SBQ + (RB / 2) * j * B_CP + c;
+    const R* Ud = sb + (sel ? 3 : 2) * SBQ + (RB / 2) * j * B_CP + c;
+    R ua[NU], ud[NU];
+#pragma unroll
+    for (int ii = 0; ii < NU; ii++) {
+      ua[ii] = Ua[ii * B_CP];
+      ud[ii] = Ud[ii * B_CP];
+    }
+    R* dst = (sel ? rd : ra) + RB * j * B_CP + c;
+#pragma unroll
+    for (int t = 0; t < RB; t++) {
+      const int par = t & 1;
+      R acc = 0;
+#pragma unroll
+      for (int n2 = 0; n2 < K; n2++) {
+        const int n = 2 * n2 + par;
+        const int ii = (t - par) / 2 - n2 + K - 1;
+        acc = fma(hr(n), ua[ii], fma(gr(n), ud[ii], acc));
+      }
+      dst[t * B_CP] = acc;
+    }
+  }
+  __syncthreads();
+  // 5. row synthesis: output row m, columns OPI j..OPI j+OPI-1 (runs of RB);
+  //    consecutive threads take consecutive rows
+#pragma unroll
+  for (int s = 0; s < C::IPT; s++) {
+    const int it = tid + s * WNT;
+    const int m = it % T, j = it / T;
+    R out[OPI];
+#pragma unroll
+    for (int hh = 0; hh < OPI / RB; hh++) {
+      const R* cl = ra + m * B_CP + (OPI / 2) * j + (RB / 2) * hh;
+      const R* ch = rd + m * B_CP + (OPI / 2) * j + (RB / 2) * hh;
+      R ua[NU], ud[NU];
+#pragma unroll
+      for (int ii = 0; ii < NU; ii++) {
+        ua[ii] = cl[ii];
+        ud[ii] = ch[ii];
+      }
+#pragma unroll
+      for (int t = 0; t < RB; t++) {
+        const int par = t & 1;
+        R acc = 0;
+#pragma unroll
+        for (int n2 = 0; n2 < K; n2++) {
+          const int n = 2 * n2 + par;
+          const int ii = (t - par) / 2 - n2 + K - 1;
+          acc = fma(hr(n), ua[ii], fma(gr(n), ud[ii], acc));
+        }
+        out[RB * hh + t] = acc;
+      }
+    }
+    emit(s, m, OPI * j, out);
+  }
+#undef hr
+#undef gr
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Issues L2 prefetches for the level coefficients (and the coarse
+// reconstruction) that level_tile_t will read for a basis of half-length K.
+template <class R, int T>
+__device__ __forceinline__ void prefetch_level(int K, const R* gto, const R* rco, int M, int N, int y0, int x0) {
+  const int CW = T / 2 + K - 1;
+  const int Mh = M / 2;
+  const int ci0 = y0 / 2 - (K - 1), cj0 = x0 / 2 - (K - 1);
+  // one prefetch per 32 coefficients of a row (128 bytes of floats)
+  const int chunks = (CW + 31) / 32;
+  for (int e = threadIdx.x; e < 4 * CW * chunks; e += WNT) {
+    const int row = e / chunks, ch = e % chunks;
+    const int qd = row / CW, i = row % CW;
+    const int gi = (ci0 + i) & (Mh - 1), gc = (cj0 + 32 * ch) & (Mh - 1);
+    if (qd == 0 && rco != nullptr) prefetch_l2(rco + (size_t)gi * Mh + gc);
+    else if (gto != nullptr) prefetch_l2(gto + (size_t)(gi + (qd >> 1) * Mh) * N + gc + (qd & 1) * Mh);
+  }
+}
+
+template <class R, int T>
+__device__ __forceinline__ void load_tile_t(const R* __restrict__ img, int M, int r0, int c0, int H, R* dst) {
+  for (int r = threadIdx.x >> 5; r < H; r += WNT / 32) {
+    const R* src = img + (size_t)((r0 + r) & (M - 1)) * M;
+    for (int c = threadIdx.x & 31; c < H; c += 32) dst[r * TC<T>::IP + c] = src[(c0 + c) & (M - 1)];
+  }
+}
+
+// One basis of level 1 on a T x T tile, adding w W_k^T U_k into the shared
+// accumulator.  Not inlined: each filter length keeps its taps as constant-bank
+// operands instead of having all lengths' taps hoisted into registers across
+// the loop over bases.
+template <class R, int T, int K, int RESID>
+__device__ __noinline__ void level1_basis(const R* in, R* ra, R* rd, R* sb, R* bacc, int N, int y0, int x0,
+                                          const R* __restrict__ gto, R* __restrict__ gtn, const R* __restrict__ rco,
+                                          IterScalars<R> sc, R w, double* q) {
+  auto emit = [&](int, int m, int x, const R* v) {
+    R* a = bacc + m * TC<T>::BP + x;
+#pragma unroll
+    for (int t = 0; t < TC<T>::OPI; t++) a[t] = fma(w, v[t], a[t]);
+  };
+  level_tile_t<R, T, K, RESID>(in, 2 * (MF_MAX_K - K), ra, rd, sb, nullptr, nullptr, N, y0, x0, gto, gtn, N, rco,
+                               sc, w, q, emit);
+}
+
+template <class R, int T, int RESID>
+__global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_level1_t(const R* __restrict__ X, R* __restrict__ b,
+                                                                  const R* __restrict__ gto, R* __restrict__ gtn,
+                                                                  const R* __restrict__ rco, int N, int L,
+                                                                  int coarsest, const WavSet<R>* __restrict__ ws,
+                                                                  IterScalars<R> sc,
+                                                                  double* __restrict__ partials) {
+  typedef TC<T> C;
+  R *ra, *rd, *sb;
+  R* in = tile_smem<R, T>(ra, rd, sb);
+  const int tpd = N / T;
+  const int band = blockIdx.y;
+  const int y0 = (blockIdx.x / tpd) * T, x0 = (blockIdx.x % tpd) * T;
+  const size_t NN = (size_t)N * N;
+  load_tile_t<R, T>(X + band * NN, N, y0 - 2 * MF_MAX_K + 2, x0 - 2 * MF_MAX_K + 2, C::IR, in);
+  for (int r = threadIdx.x; r < T * (T / 32); r += WNT)  // the b tile read at the end
+    prefetch_l2(b + band * NN + (size_t)(y0 + r / (T / 32)) * N + x0 + 32 * (r % (T / 32)));
+  if (ws->nd > 0)
+    prefetch_level<R, T>(ws->K[0], gto + (size_t)band * NN, coarsest ? nullptr : rco + (size_t)band * (NN / 4), N,
+                         N, y0, x0);
+  double q[Q_COUNT];
+#pragma unroll
+  for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
+  q[Q_XMIN] = 1e300;
+  // the weighted sum over bases accumulates in shared memory; each thread owns
+  // the same outputs for every basis
+  R* bacc = sb + 4 * C::SBQ;
+  for (int e = threadIdx.x; e < T * C::BP; e += WNT) bacc[e] = 0;
+  __syncthreads();
+  const int nd = ws->nd;
+  for (int k = 0; k < nd; k++) {
+    const size_t gofs = ((size_t)k * L + band) * NN;
+    const R* rc = coarsest ? nullptr : rco + ((size_t)k * L + band) * (NN / 4);
+    const R w = ws->w[k];
+    if (k + 1 < nd) {
+      const size_t g1 = ((size_t)(k + 1) * L + band) * NN;
+      prefetch_level<R, T>(ws->K[k + 1], gto + g1,
+                           coarsest ? nullptr : rco + ((size_t)(k + 1) * L + band) * (NN / 4), N, N, y0, x0);
+    }
+    MF_K_SWITCH(ws->K[k], (level1_basis<R, T, KK, RESID>(in, ra, rd, sb, bacc, N, y0, x0, gto + gofs, gtn + gofs,
+                                                         rc, sc, w, q)));
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < T * T; e += WNT) {
+    const int m = e / T, x = e % T;
+    R* dst = b + band * NN + (size_t)(y0 + m) * N + x0 + x;
+    *dst += bacc[m * C::BP + x];
+  }
+  if (RESID) block_reduce_write<WNT>(q, partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * MF_NQ);
+}
+
+template <class R, int T, int RESID>
+__global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_levelj_t(const R* __restrict__ in_img,
+                                                                  R* __restrict__ out_img,
+                                                                  const R* __restrict__ gto, R* __restrict__ gtn,
+                                                                  const R* __restrict__ rco, int N, int M, int L,
+                                                                  int coarsest, const WavSet<R>* __restrict__ ws,
+                                                                  IterScalars<R> sc,
+                                                                  double* __restrict__ partials) {
+  R *ra, *rd, *sb;
+  R* in = tile_smem<R, T>(ra, rd, sb);
+  const int tpd = M / T;
+  const int band = blockIdx.y, k = blockIdx.z;
+  const int y0 = (blockIdx.x / tpd) * T, x0 = (blockIdx.x % tpd) * T;
+  const size_t MM = (size_t)M * M;
+  const R* src = in_img + ((size_t)k * L + band) * MM;
+  R* dst = out_img + ((size_t)k * L + band) * MM;
+  const size_t gofs = ((size_t)k * L + band) * (size_t)N * N;
+  const R* rc = coarsest ? nullptr : rco + ((size_t)k * L + band) * (MM / 4);
+  double q[Q_COUNT];
+#pragma unroll
+  for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
+  q[Q_XMIN] = 1e300;
+  const R w = ws->w[k];
+  auto emit = [&](int, int m, int x, const R* v) {
+    R* o = dst + (size_t)(y0 + m) * M + x0 + x;
+#pragma unroll
+    for (int t = 0; t < TC<T>::OPI; t++) o[t] = v[t];
+  };
+  prefetch_level<R, T>(ws->K[k], gto + gofs, rc, M, N, y0, x0);
+  MF_K_SWITCH(ws->K[k], {
+    load_tile_t<R, T>(src, M, y0 - 2 * KK + 2, x0 - 2 * KK + 2, T + 4 * KK - 4, in);
+    __syncthreads();
+    level_tile_t<R, T, KK, RESID>(in, 0, ra, rd, sb, nullptr, nullptr, M, y0, x0, gto + gofs, gtn + gofs, N, rc,
+                                  sc, w, q, emit);
+  });
+  if (RESID)
+    block_reduce_write<WNT>(
+        q, partials + (((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * MF_NQ);
+}
+
 // Low-low analysis: LL_j (M/2 x M/2) of the M x M input, for one basis per CTA
 // or (shared input, in_basis_stride == 0) for every basis in one CTA.
 template <class R, int K>
@@ -290,6 +723,41 @@ __device__ __forceinline__ void ll_tile(const R* in, R* a, int TO, const R* __re
 #pragma unroll
   for (int n = 0; n < F; n++) hr[n] = h[n];
   const int IH = 2 * TO + F - 2;
+  if (TO == LT) {
+    // rows: 8 consecutive low-pass outputs per thread from 14 + F inputs
+    for (int it = threadIdx.x; it < IH * (LT / 8); it += WNT) {
+      const int r = it / (LT / 8), j = it % (LT / 8);
+      const R* src = in + r * LIM + 16 * j;
+      R v[14 + F];
+#pragma unroll
+      for (int t = 0; t < 14 + F; t++) v[t] = src[t];
+#pragma unroll
+      for (int c = 0; c < 8; c++) {
+        R acc = 0;
+#pragma unroll
+        for (int n = 0; n < F; n++) acc = fma(hr[n], v[2 * c + n], acc);
+        a[r * LT + 8 * j + c] = acc;
+      }
+    }
+    __syncthreads();
+    // columns: 4 consecutive outputs per thread from 6 + F inputs
+    for (int it = threadIdx.x; it < LT * (LT / 4); it += WNT) {
+      const int c = it % LT, j = it / LT;
+      const R* col = a + 8 * j * LT + c;
+      R v[6 + F];
+#pragma unroll
+      for (int t = 0; t < 6 + F; t++) v[t] = col[t * LT];
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        R acc = 0;
+#pragma unroll
+        for (int n = 0; n < F; n++) acc = fma(hr[n], v[2 * i + n], acc);
+        dst[(size_t)(oy + 4 * j + i) * Mo + ox + c] = acc;
+      }
+    }
+    __syncthreads();
+    return;
+  }
   for (int e = threadIdx.x; e < IH * TO; e += WNT) {
     const int r = e / TO, c = e % TO;
     const R* src = in + r * LIM + 2 * c;
@@ -345,9 +813,17 @@ __global__ void __launch_bounds__(WNT) k_wav_ll(const R* __restrict__ in_img, si
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// Output tile edge of the fused level kernels: the largest of the allowed
+// sizes (pref, 32, or the generic small-tile path) that divides M.
+static int level_tile_edge(int M, int pref) {
+  if (pref >= 64 && M >= 64) return 64;
+  if (M >= 32) return 32;
+  return M < WT ? M : WT;
+}
+
 template <class R>
-int wav_level_blocks(int M, int L, int nd) {
-  const int T = M < WT ? M : WT;
+int wav_level_blocks(int M, int L, int nd, int pref) {
+  const int T = level_tile_edge(M, pref);
   const int tiles = (M / T) * (M / T);
   return tiles * L * nd;
 }
@@ -366,48 +842,71 @@ cudaError_t launch_wav_ll(const R* in, size_t in_band_stride, size_t in_basis_st
   return cudaGetLastError();
 }
 
-template <class R>
-cudaError_t launch_wav_level(const R* in, size_t, size_t, const R* rcoarse, R* out, const R* gt_old, R* gt_new,
-                             int N, int M, int L, int coarsest, int nd, const WavSet<R>* ws, IterScalars<R> sc,
-                             double* partials, int resid, cudaStream_t s) {
-  const int T = M < WT ? M : WT;
-  const int tiles = (M / T) * (M / T);
-  const size_t sm = sizeof(R) * (IHM * IHM + 2 * IHM * CWM + 4 * CWM * CWM);
-  cudaError_t e;
-  if (M == N) {
-    dim3 grid(tiles, L);
-    if (resid) {
-      e = cudaFuncSetAttribute(k_wav_level1<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e != cudaSuccess) return e;
-      k_wav_level1<R, 1><<<grid, WNT, sm, s>>>(in, out, gt_old, gt_new, rcoarse, N, L, coarsest, ws, sc, partials);
-    } else {
-      e = cudaFuncSetAttribute(k_wav_level1<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e != cudaSuccess) return e;
-      k_wav_level1<R, 0><<<grid, WNT, sm, s>>>(in, out, gt_old, gt_new, rcoarse, N, L, coarsest, ws, sc, partials);
-    }
-  } else {
-    dim3 grid(tiles, L, nd);
-    if (resid) {
-      e = cudaFuncSetAttribute(k_wav_levelj<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e != cudaSuccess) return e;
-      k_wav_levelj<R, 1><<<grid, WNT, sm, s>>>(in, out, gt_old, gt_new, rcoarse, N, M, L, coarsest, ws, sc,
-                                               partials);
-    } else {
-      e = cudaFuncSetAttribute(k_wav_levelj<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e != cudaSuccess) return e;
-      k_wav_levelj<R, 0><<<grid, WNT, sm, s>>>(in, out, gt_old, gt_new, rcoarse, N, M, L, coarsest, ws, sc,
-                                               partials);
-    }
-  }
+template <class R, class Kern, class... Args>
+static cudaError_t launch_k(Kern kern, dim3 grid, size_t sm, cudaStream_t s, Args... args) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, WNT, sm, s>>>(args...);
   return cudaGetLastError();
 }
 
+template <class R, int T>
+static cudaError_t launch_level_t(const R* in, const R* rcoarse, R* out, const R* gt_old, R* gt_new, int N, int M,
+                                  int L, int coarsest, int nd, const WavSet<R>* ws, IterScalars<R> sc,
+                                  double* partials, int resid, cudaStream_t s) {
+  const int tiles = (M / T) * (M / T);
+  if (M == N) {
+    dim3 grid(tiles, L);
+    const size_t sm1 = sizeof(R) * TC<T>::SMEM1;
+    if (resid)
+      return launch_k<R>(k_wav_level1_t<R, T, 1>, grid, sm1, s, in, out, gt_old, gt_new, rcoarse, N, L, coarsest, ws,
+                         sc, partials);
+    return launch_k<R>(k_wav_level1_t<R, T, 0>, grid, sm1, s, in, out, gt_old, gt_new, rcoarse, N, L, coarsest, ws,
+                       sc, partials);
+  }
+  dim3 grid(tiles, L, nd);
+  const size_t sm = sizeof(R) * TC<T>::SMEM;
+  if (resid)
+    return launch_k<R>(k_wav_levelj_t<R, T, 1>, grid, sm, s, in, out, gt_old, gt_new, rcoarse, N, M, L, coarsest, ws,
+                       sc, partials);
+  return launch_k<R>(k_wav_levelj_t<R, T, 0>, grid, sm, s, in, out, gt_old, gt_new, rcoarse, N, M, L, coarsest, ws,
+                     sc, partials);
+}
+
+template <class R>
+cudaError_t launch_wav_level(const R* in, size_t, size_t, const R* rcoarse, R* out, const R* gt_old, R* gt_new,
+                             int N, int M, int L, int coarsest, int nd, const WavSet<R>* ws, IterScalars<R> sc,
+                             double* partials, int resid, int pref_tile, cudaStream_t s) {
+  const int T = level_tile_edge(M, pref_tile);
+  if (T == 64)
+    return launch_level_t<R, 64>(in, rcoarse, out, gt_old, gt_new, N, M, L, coarsest, nd, ws, sc, partials, resid, s);
+  if (T == 32)
+    return launch_level_t<R, 32>(in, rcoarse, out, gt_old, gt_new, N, M, L, coarsest, nd, ws, sc, partials, resid, s);
+  const int tiles = (M / T) * (M / T);
+  const size_t sm = sizeof(R) * (IHM * IHM + 2 * IHM * CWM + 4 * CWM * CWM);
+  if (M == N) {
+    dim3 grid(tiles, L);
+    if (resid)
+      return launch_k<R>(k_wav_level1<R, 1>, grid, sm, s, in, out, gt_old, gt_new, rcoarse, N, L, coarsest, ws, sc,
+                         partials);
+    return launch_k<R>(k_wav_level1<R, 0>, grid, sm, s, in, out, gt_old, gt_new, rcoarse, N, L, coarsest, ws, sc,
+                       partials);
+  }
+  dim3 grid(tiles, L, nd);
+  if (resid)
+    return launch_k<R>(k_wav_levelj<R, 1>, grid, sm, s, in, out, gt_old, gt_new, rcoarse, N, M, L, coarsest, ws, sc,
+                       partials);
+  return launch_k<R>(k_wav_levelj<R, 0>, grid, sm, s, in, out, gt_old, gt_new, rcoarse, N, M, L, coarsest, ws, sc,
+                     partials);
+}
+
 #define INST(R)                                                                                               \
-  template int wav_level_blocks<R>(int, int, int);                                                           \
+  template int wav_level_blocks<R>(int, int, int, int);                                                           \
   template cudaError_t launch_wav_ll<R>(const R*, size_t, size_t, R*, int, int, int, const WavSet<R>*,            \
                                         cudaStream_t);                                                          \
   template cudaError_t launch_wav_level<R>(const R*, size_t, size_t, const R*, R*, const R*, R*, int, int, int,   \
-                                           int, int, const WavSet<R>*, IterScalars<R>, double*, int, cudaStream_t);
+                                           int, int, const WavSet<R>*, IterScalars<R>, double*, int, int,        \
+                                           cudaStream_t);
 INST(float)
 INST(double)
 #undef INST
