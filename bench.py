@@ -204,6 +204,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="splitbf16", choices=["splitbf16", "fp32"],
+                    help="DCT arithmetic of the spectral step (the cube is FP32 either way)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -235,13 +237,14 @@ def main():
     N, L = cube.y.shape[-1], cube.y.shape[0]
     V = N * N * L
     prm = synth.WORKLOAD_PARAMS
+    precision = mf.MF_FP32_DCT_SPLITBF16 if args.precision == "splitbf16" else mf.MF_FP32
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         psf = torch.tensor(cube.psf, dtype=torch.float32, device="cuda")
         y = torch.tensor(cube.y, dtype=torch.float32, device="cuda")
         plan = mf.Plan(psf)
-        params = plan.params(stream=stream.cuda_stream, **prm)
-        params_warm = plan.params(stream=stream.cuda_stream, warm_start=1, **prm)
+        params = plan.params(stream=stream.cuda_stream, precision=precision, **prm)
+        params_warm = plan.params(stream=stream.cuda_stream, warm_start=1, precision=precision, **prm)
         plan.iterate(y, args.warmup, params)
     stream.synchronize()
 
@@ -269,7 +272,7 @@ def main():
     # pinned host memory, runs one iteration with the FP64 residual report, reads it back ---
     y_host = torch.tensor(cube.y, dtype=torch.float32).pin_memory()
     y_dev = torch.empty_like(y)
-    params_e2e = plan.params(stream=stream.cuda_stream, warm_start=1, resid_every=1, **prm)
+    params_e2e = plan.params(stream=stream.cuda_stream, warm_start=1, resid_every=1, precision=precision, **prm)
     e2e_steps = max(3, min(args.steps, 10))
     barrier()
     t0 = time.perf_counter()
@@ -315,8 +318,9 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f32+bf16x3", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "L": L, "wavelet_levels": 3, "bases": "Db1-Db8+Haar",
+                   "dct": "split-BF16 tcgen05, FP32 accumulate" if args.precision == "splitbf16" else "FP32",
                    "n_iter_per_step": 1, "parallelism": "replicas" if world > 1 else "single",
                    "l2": f"inputs larger than L2 (plan working set {plan.device_bytes / 1e9:.1f} GB)",
                    "params": prm},

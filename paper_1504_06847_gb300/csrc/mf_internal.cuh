@@ -93,6 +93,8 @@ struct mf_plan {
   size_t partial_cap;
   double* sums;      // [MF_NQ] device
   void* wset;        // WavSet of the current call (device)
+  void* dct_tc;      // split-BF16 DCT operands of the precision form (device), or null
+  int* err;          // device error word (bounded waits that expired)
   size_t total_bytes;
   cudaStream_t stream;
   mf_status status;
@@ -152,6 +154,15 @@ template <class R> cudaError_t launch_wav_level(const R* in, size_t in_band_stri
                                                 IterScalars<R> sc, double* partials, int resid, int pref_tile,
                                                 cudaStream_t s);
 template <class R> int wav_level_blocks(int M, int L, int nd, int pref_tile);
+// Precision form of the spectral step: DCTs as split-BF16 tcgen05 products (L <= 64).
+int spectral_tc_lp_of(int L);                        // padded L (16, 32, 48, 64) or 0
+size_t spectral_tc_operand_elems(int L);             // BF16 elements of the DCT operands
+void spectral_tc_build_operands(int L, uint16_t* out);  // host: C and C^T split hi/lo, core layout
+cudaError_t launch_spectral_tc(const float* X, float* GP, float* Sd, float* GV, float* GSd, float* b,
+                               const uint16_t* bmats, int N, int L, IterScalars<float> sc, double* partials,
+                               int resid, int* err, cudaStream_t s);
+int spectral_tc_blocks(int N);
+
 // Copies the Daubechies tap tables into the wavelet kernels' constant memory
 // (current device; the values are the same for every plan).
 cudaError_t upload_taps();

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "mf_internal.cuh"
 
@@ -92,7 +93,7 @@ struct Alloc {
 void free_plan_memory(mf_plan* p) {
   void* ptrs[] = {p->X, p->b, p->GP, p->Sd, p->GV, p->GSd, p->GT[0], p->GT[1], p->work, p->hhat, p->hhat_nyq,
                   p->yhat, p->yhat_nyq, p->cc, p->cc_nyq, p->gg, p->gg_nyq, p->tw, p->dctC, p->scratch,
-                  p->partials, p->sums, p->wset};
+                  p->partials, p->sums, p->wset, p->dct_tc, p->err};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
@@ -160,6 +161,8 @@ mf_status create(int N, int L, const R* psf, mf_plan** out) {
   p->partials = (double*)a.get(cap * MF_NQ * sizeof(double));
   p->sums = (double*)a.get(MF_NQ * sizeof(double));
   p->wset = a.get(sizeof(WavSet<R>));
+  p->err = (int*)a.get(sizeof(int));
+  if (sizeof(R) == 4 && spectral_tc_lp_of(L) > 0) p->dct_tc = a.get(spectral_tc_operand_elems(L) * sizeof(uint16_t));
   if (!a.ok) {
     free_plan_memory(p);
     delete p;
@@ -181,6 +184,12 @@ mf_status create(int N, int L, const R* psf, mf_plan** out) {
     cudaError_t e1 = cudaMemcpy(p->tw, tw, sizeof(cx<R>) * N, cudaMemcpyHostToDevice);
     cudaError_t e2 = cudaMemcpy(p->dctC, C, sizeof(R) * L * L, cudaMemcpyHostToDevice);
     cudaError_t e3 = upload_taps();
+    if (e3 == cudaSuccess) e3 = cudaMemset(p->err, 0, sizeof(int));
+    if (e3 == cudaSuccess && p->dct_tc) {
+      std::vector<uint16_t> ops(spectral_tc_operand_elems(L));
+      spectral_tc_build_operands(L, ops.data());
+      e3 = cudaMemcpy(p->dct_tc, ops.data(), ops.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+    }
     delete[] tw;
     delete[] C;
     if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
@@ -218,7 +227,13 @@ mf_status check_params(const mf_plan* p, const mf_params* prm, int n_iter, int w
   if (J < 1 || (p->N >> J) < 2) return MF_ERR_INVALID;
   if (prm->wavelet_mask == 0 || (prm->wavelet_mask >> 9) != 0) return MF_ERR_INVALID;
   if (prm->resid_every < 0) return MF_ERR_INVALID;
-  if (p->dbl ? prm->precision != MF_FP64 : (prm->precision != MF_FP32)) return MF_ERR_INVALID;
+  if (p->dbl) {
+    if (prm->precision != MF_FP64) return MF_ERR_INVALID;
+  } else if (prm->precision == MF_FP32_DCT_SPLITBF16) {
+    if (!p->dct_tc) return MF_ERR_INVALID;  // needs L <= 64
+  } else if (prm->precision != MF_FP32) {
+    return MF_ERR_INVALID;
+  }
   return MF_OK;
 }
 
@@ -250,8 +265,29 @@ WavSet<R> make_wavset(unsigned mask, int* n_s) {
 }
 
 template <class R>
+cudaError_t spectral_step(mf_plan* p, const IterScalars<R>& sc, int resid, int precision, cudaStream_t s) {
+  return launch_spectral<R>((const R*)p->X, (R*)p->GP, (R*)p->Sd, (R*)p->GV, (R*)p->GSd, (R*)p->b,
+                            (const R*)p->dctC, p->N, p->L, sc, p->partials, resid, s);
+}
+template <>
+cudaError_t spectral_step<float>(mf_plan* p, const IterScalars<float>& sc, int resid, int precision,
+                                 cudaStream_t s) {
+  if (precision == MF_FP32_DCT_SPLITBF16)
+    return launch_spectral_tc((const float*)p->X, (float*)p->GP, (float*)p->Sd, (float*)p->GV, (float*)p->GSd,
+                              (float*)p->b, (const uint16_t*)p->dct_tc, p->N, p->L, sc, p->partials, resid, p->err,
+                              s);
+  return launch_spectral<float>((const float*)p->X, (float*)p->GP, (float*)p->Sd, (float*)p->GV, (float*)p->GSd,
+                                (float*)p->b, (const float*)p->dctC, p->N, p->L, sc, p->partials, resid, s);
+}
+
+template <class R>
+int spectral_grid(const mf_plan* p, int precision) {
+  return precision == MF_FP32_DCT_SPLITBF16 ? spectral_tc_blocks(p->N) : spectral_blocks<R>(p->N, p->L);
+}
+
+template <class R>
 cudaError_t iteration(mf_plan* p, int J, int nd, const WavSet<R>* wsd, const IterScalars<R>& sc, int resid,
-                      cudaStream_t s) {
+                      int precision, cudaStream_t s) {
   const int N = p->N, L = p->L;
   const size_t NN = (size_t)N * N;
   cudaError_t e;
@@ -279,13 +315,11 @@ cudaError_t iteration(mf_plan* p, int J, int nd, const WavSet<R>* wsd, const Ite
   // steps II, IV, V (+ duals), pointwise part of b
   {
     Timed t(p, MF_K_SPECTRAL, s);
-    if ((e = launch_spectral<R>((const R*)p->X, (R*)p->GP, (R*)p->Sd, (R*)p->GV, (R*)p->GSd, (R*)p->b,
-                                (const R*)p->dctC, N, L, sc, p->partials, resid, s)))
-      return e;
+    if ((e = spectral_step<R>(p, sc, resid, precision, s))) return e;
   }
   if (resid) {
     Timed t(p, MF_K_REDUCE, s);
-    if ((e = launch_finalize(p->partials, spectral_blocks<R>(N, L), p->sums, 1, s))) return e;
+    if ((e = launch_finalize(p->partials, spectral_grid<R>(p, precision), p->sums, 1, s))) return e;
   }
   // step III (+ dual), wavelet part of b
   R* scr = (R*)p->scratch;
@@ -383,7 +417,7 @@ mf_status iterate(mf_plan* p, const R* y, const mf_params* prm, int n_iter) {
   const int J = prm->wavelet_levels;
   for (int it = 0; it < n_iter && !e; it++) {
     const int resid = prm->resid_every > 0 && (((it + 1) % prm->resid_every) == 0 || it == n_iter - 1);
-    e = iteration<R>(p, J, ws.nd, (const WavSet<R>*)p->wset, sc, resid, s);
+    e = iteration<R>(p, J, ws.nd, (const WavSet<R>*)p->wset, sc, resid, prm->precision, s);
     if (!e && resid) {
       p->report_pending = 1;
       p->report.resid_iter = p->iters_done + it + 1;
@@ -532,6 +566,14 @@ mf_status mf_plan_get_report(mf_plan* p, mf_report* r) {
   if (cudaStreamSynchronize(p->stream) != cudaSuccess) {
     p->status = MF_ERR_CUDA;
     return p->status;
+  }
+  {
+    int err = 0;
+    if (cudaMemcpy(&err, p->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      p->status = MF_ERR_CUDA;
+      return p->status;
+    }
+    if (err && p->status == MF_OK) p->status = MF_ERR_TIMEOUT;
   }
   if (p->report_pending) {
     double q[MF_NQ];
