@@ -108,6 +108,17 @@ size_t mf_plan_device_bytes(const mf_plan* p);
 mf_status mf_admm_iterate(mf_plan* p, const float* y_cube, const mf_params* prm, int n_iter);
 mf_status mf_admm_iterate_f64(mf_plan* p, const double* y_cube, const mf_params* prm, int n_iter);
 
+/* Batched form: runs n_iter iterations of Algorithm 1 on each of `count`
+ * independent FP32 plans (cubes of any N and L; no plan may appear twice),
+ * plan i on the dirty cube y_cubes[i] (device pointers), as ONE CUDA graph
+ * launch on prm->stream in which every cube is its own branch.  The graph is
+ * built and instantiated on each call (host cost) and kept by plans[0] until
+ * its next batch call or its destruction.  Per-plan results, state access and
+ * reports are as after mf_admm_iterate.  Per-kernel event timing is suspended
+ * inside the graph.  Errors: MF_ERR_INVALID, MF_ERR_CUDA (latched in every plan). */
+mf_status mf_batch_iterate(mf_plan* const* plans, const float* const* y_cubes, int count, const mf_params* prm,
+                           int n_iter);
+
 /* Which state array to read or write (all [L][N][N] unless noted). */
 typedef enum {
   MF_ARR_X = 0,        /* X after the last step I (Algorithm 1 returns X) */

@@ -23,7 +23,7 @@ EXPORTS = ["mf_params_default", "mf_plan_create", "mf_plan_create_f64", "mf_plan
            "mf_plan_device_bytes", "mf_admm_iterate", "mf_admm_iterate_f64", "mf_plan_get_array",
            "mf_plan_set_array", "mf_plan_get_state", "mf_plan_set_state", "mf_plan_get_report",
            "mf_wavelet_filter", "mf_status_string", "mf_plan_set_timing", "mf_plan_get_timing",
-           "mf_kernel_name", "mf_xstep_noalloc", "mf_plan_set_option"]
+           "mf_kernel_name", "mf_xstep_noalloc", "mf_plan_set_option", "mf_batch_iterate"]
 MF_OPT_WAV_TILE = 0
 
 KERNELS = ["rows_fwd", "cols_solve", "rows_inv", "spectral", "wav_ll", "wav_level1", "wav_levelj", "setup",
@@ -101,6 +101,9 @@ def lib():
         L.mf_plan_get_timing.restype = ctypes.c_int
         L.mf_kernel_name.argtypes = [ctypes.c_int]
         L.mf_kernel_name.restype = ctypes.c_char_p
+        L.mf_batch_iterate.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(Params),
+                                       ctypes.c_int]
+        L.mf_batch_iterate.restype = ctypes.c_int
         L.mf_plan_set_option.argtypes = [vp, ctypes.c_int, ctypes.c_int]
         L.mf_plan_set_option.restype = ctypes.c_int
         L.mf_xstep_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.POINTER(Params), vp]
@@ -134,6 +137,29 @@ def wavelet_filter(K: int):
     n = ctypes.c_int()
     _check(lib().mf_wavelet_filter(K, taps, ctypes.byref(n)), "mf_wavelet_filter")
     return [taps[i] for i in range(n.value)]
+
+
+def batch_iterate(plans, ys, n_iter: int, **kw):
+    """Batched form: n_iter iterations of every (plan, y) pair in one CUDA graph
+    launch (see mf_batch_iterate).  FP32 plans; ys are CUDA tensors [L, N, N]."""
+    import torch
+
+    if len(plans) != len(ys) or not plans:
+        raise ValueError("one dirty cube per plan")
+    for p_, y in zip(plans, ys):
+        if p_.dtype != torch.float32:
+            raise ValueError("the batched form takes FP32 plans")
+        if y.dtype != torch.float32 or not y.is_cuda or tuple(y.shape) != (p_.L, p_.N, p_.N):
+            raise ValueError("each y must be a float32 CUDA tensor matching its plan")
+    ys = [y.contiguous() for y in ys]
+    if "stream" not in kw:
+        kw["stream"] = torch.cuda.current_stream(ys[0].device).cuda_stream
+    prm = default_params(**kw)
+    hp = (ctypes.c_void_p * len(plans))(*[p_._h.value for p_ in plans])
+    yp = (ctypes.c_void_p * len(ys))(*[y.data_ptr() for y in ys])
+    _check(lib().mf_batch_iterate(hp, yp, len(plans), ctypes.byref(prm), int(n_iter)), "mf_batch_iterate")
+    for p_, y in zip(plans, ys):
+        p_._y_keepalive = y
 
 
 def xstep_noalloc(psf, y, b, x_out, **kw):

@@ -104,6 +104,8 @@ struct mf_plan {
   double rho_weights[4];
   mf_params last_params;
   int wav_tile;         // preferred wavelet tile edge (MF_OPT_WAV_TILE)
+  void* batch_exec;     // last batch graph launched with this plan first (cudaGraphExec_t)
+  cudaStream_t batch_stream;
   // per-kernel timing
   int timing;
   long long launches[MF_K_COUNT];

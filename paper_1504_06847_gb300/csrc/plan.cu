@@ -366,13 +366,15 @@ cudaError_t iteration(mf_plan* p, int J, int nd, const WavSet<R>* wsd, const Ite
   return cudaSuccess;
 }
 
+// Per-call part of an iterate: validation, the wavelet set, Fourier constants
+// F(y), g, c and (unless warm) the zero state, enqueued on s.
 template <class R>
-mf_status iterate(mf_plan* p, const R* y, const mf_params* prm, int n_iter) {
+mf_status prepare(mf_plan* p, const R* y, const mf_params* prm, int n_iter, cudaStream_t s, WavSet<R>* ws_out,
+                  IterScalars<R>* sc_out) {
   mf_status st = check_params(p, prm, n_iter, sizeof(R) == 8);
   if (st != MF_OK) return st;
   if (!y) return MF_ERR_INVALID;
   if (p->status != MF_OK) return p->status;
-  cudaStream_t s = (cudaStream_t)prm->stream;
   p->stream = s;
   const int N = p->N, L = p->L;
   int n_s = 0;
@@ -413,20 +415,33 @@ mf_status iterate(mf_plan* p, const R* y, const mf_params* prm, int n_iter) {
       p->report.resid_iter = -1;
     }
   }
+  if (e) {
+    p->status = MF_ERR_CUDA;
+    return p->status;
+  }
   p->nd_state = ws.nd;
-  const int J = prm->wavelet_levels;
+  *ws_out = ws;
+  *sc_out = sc;
+  return MF_OK;
+}
+
+// n_iter iterations enqueued on s (also under stream capture).
+template <class R>
+cudaError_t run_iterations(mf_plan* p, const mf_params* prm, int n_iter, const WavSet<R>& ws,
+                           const IterScalars<R>& sc, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
   for (int it = 0; it < n_iter && !e; it++) {
     const int resid = prm->resid_every > 0 && (((it + 1) % prm->resid_every) == 0 || it == n_iter - 1);
-    e = iteration<R>(p, J, ws.nd, (const WavSet<R>*)p->wset, sc, resid, prm->precision, s);
+    e = iteration<R>(p, prm->wavelet_levels, ws.nd, (const WavSet<R>*)p->wset, sc, resid, prm->precision, s);
     if (!e && resid) {
       p->report_pending = 1;
       p->report.resid_iter = p->iters_done + it + 1;
     }
   }
-  if (e) {
-    p->status = MF_ERR_CUDA;
-    return p->status;
-  }
+  return e;
+}
+
+void finish(mf_plan* p, const mf_params* prm, int n_iter) {
   p->iters_done += n_iter;
   p->rho_weights[0] = prm->rho_P;
   p->rho_weights[1] = prm->rho_T;
@@ -434,6 +449,104 @@ mf_status iterate(mf_plan* p, const R* y, const mf_params* prm, int n_iter) {
   p->rho_weights[3] = prm->rho_S;
   p->report.iters_done = p->iters_done;
   std::memcpy(&p->last_params, prm, sizeof(mf_params));
+}
+
+template <class R>
+mf_status iterate(mf_plan* p, const R* y, const mf_params* prm, int n_iter) {
+  cudaStream_t s = prm ? (cudaStream_t)prm->stream : nullptr;
+  WavSet<R> ws;
+  IterScalars<R> sc;
+  mf_status st = prepare<R>(p, y, prm, n_iter, s, &ws, &sc);
+  if (st != MF_OK) return st;
+  if (run_iterations<R>(p, prm, n_iter, ws, sc, s) != cudaSuccess) {
+    cudaGetLastError();
+    p->status = MF_ERR_CUDA;
+    return p->status;
+  }
+  finish(p, prm, n_iter);
+  return MF_OK;
+}
+
+// Batched form: every plan's n_iter iterations in one CUDA graph, each cube on
+// its own branch, launched once on prm->stream.
+mf_status batch_iterate(mf_plan* const* plans, const float* const* ys, int count, const mf_params* prm,
+                        int n_iter) {
+  if (!plans || !ys || !prm || count < 1 || count > 1024 || n_iter < 1) return MF_ERR_INVALID;
+  for (int i = 0; i < count; i++) {
+    if (!plans[i] || plans[i]->dbl || !ys[i]) return MF_ERR_INVALID;
+    for (int j = 0; j < i; j++)
+      if (plans[j] == plans[i]) return MF_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)prm->stream;
+  mf_plan* owner = plans[0];
+  if (owner->batch_exec) {  // the previous batch graph of this owner
+    if (cudaStreamSynchronize(owner->batch_stream) != cudaSuccess) return MF_ERR_CUDA;
+    cudaGraphExecDestroy((cudaGraphExec_t)owner->batch_exec);
+    owner->batch_exec = nullptr;
+  }
+  std::vector<WavSet<float>> ws(count);
+  std::vector<IterScalars<float>> sc(count);
+  for (int i = 0; i < count; i++) {
+    mf_status st = prepare<float>(plans[i], ys[i], prm, n_iter, s, &ws[i], &sc[i]);
+    if (st != MF_OK) return st;
+  }
+  // The graph is recorded on a private stream (the caller's may be the legacy
+  // default stream, which cannot be captured) and launched on the caller's.
+  std::vector<cudaStream_t> side(count, nullptr);
+  std::vector<cudaEvent_t> join(count, nullptr);
+  cudaEvent_t fork = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int> timing(count);
+  cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (!e) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  for (int i = 0; i < count && !e; i++) {
+    e = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking);
+    if (!e) e = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+    timing[i] = plans[i]->timing;
+    plans[i]->timing = 0;  // no event brackets inside the graph
+  }
+  bool capturing = false;
+  if (!e) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (!e) {
+    capturing = true;
+    e = cudaEventRecord(fork, cap);
+  }
+  for (int i = 0; i < count && !e; i++) {
+    e = cudaStreamWaitEvent(side[i], fork, 0);
+    if (!e) e = run_iterations<float>(plans[i], prm, n_iter, ws[i], sc[i], side[i]);
+    if (!e) e = cudaEventRecord(join[i], side[i]);
+    if (!e) e = cudaStreamWaitEvent(cap, join[i], 0);
+  }
+  if (capturing) {
+    cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+    if (!e) e = e2;
+  }
+  if (!e) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (!e) e = cudaGraphLaunch(exec, s);
+  for (int i = 0; i < count; i++) {
+    plans[i]->timing = timing[i];
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (fork) cudaEventDestroy(fork);
+  if (cap) cudaStreamDestroy(cap);
+  for (int i = 0; i < count; i++) {
+    if (join[i]) cudaEventDestroy(join[i]);
+    if (side[i]) cudaStreamDestroy(side[i]);
+  }
+  if (e) {
+    cudaGetLastError();
+    if (exec) cudaGraphExecDestroy(exec);
+    for (int i = 0; i < count; i++) plans[i]->status = MF_ERR_CUDA;
+    return MF_ERR_CUDA;
+  }
+  owner->batch_exec = exec;
+  owner->batch_stream = s;
+  for (int i = 0; i < count; i++) {
+    finish(plans[i], prm, n_iter);
+    plans[i]->stream = s;
+  }
   return MF_OK;
 }
 
@@ -486,6 +599,7 @@ mf_status mf_plan_create_f64(int N, int L, const double* psf_cube, mf_plan** out
 void mf_plan_destroy(mf_plan* p) {
   if (!p) return;
   cudaDeviceSynchronize();
+  if (p->batch_exec) cudaGraphExecDestroy((cudaGraphExec_t)p->batch_exec);
   free_plan_memory(p);
   delete p;
 }
@@ -497,6 +611,11 @@ mf_status mf_admm_iterate(mf_plan* p, const float* y, const mf_params* prm, int 
 }
 mf_status mf_admm_iterate_f64(mf_plan* p, const double* y, const mf_params* prm, int n_iter) {
   return iterate<double>(p, y, prm, n_iter);
+}
+
+mf_status mf_batch_iterate(mf_plan* const* plans, const float* const* y_cubes, int count, const mf_params* prm,
+                           int n_iter) {
+  return batch_iterate(plans, y_cubes, count, prm, n_iter);
 }
 
 mf_status mf_plan_get_array(mf_plan* p, int which, void* dst, size_t* count) {
