@@ -119,6 +119,21 @@ mf_status mf_admm_iterate_f64(mf_plan* p, const double* y_cube, const mf_params*
 mf_status mf_batch_iterate(mf_plan* const* plans, const float* const* y_cubes, int count, const mf_params* prm,
                            int n_iter);
 
+/* Differentiable form (reverse mode of the unrolled iteration).  Runs n_iter
+ * iterations of Algorithm 1 from the zero state on y_cube with the four
+ * penalties tied (prm->rho_P = rho_T = rho_V = rho_S = rho; FP32 plan,
+ * MF_FP32, L <= 64, warm_start 0), checkpointing every iteration, then sweeps
+ * back: given dL_dX = dL/dX (device [L][N][N]) for the X of the last step I,
+ * writes dL/dy into dL_dy (device [L][N][N]) and dL/dmu_s, dL/dmu_nu, dL/drho
+ * into the host doubles (any may be NULL).  Subgradients: the derivative of
+ * max(0, t) and of the soft threshold in t is 1 only where the inequality is
+ * strict.  Allocates the checkpoints ((5 + nd) cubes per iteration) and
+ * (8 + 3 nd) work cubes for the call and synchronises prm->stream before
+ * returning; afterwards the plan holds the forward's final state.
+ * Errors: MF_ERR_INVALID, MF_ERR_OOM, MF_ERR_CUDA. */
+mf_status mf_admm_backward(mf_plan* p, const float* y_cube, const mf_params* prm, int n_iter, const float* dL_dX,
+                           float* dL_dy, double* dL_dmu_s, double* dL_dmu_nu, double* dL_drho);
+
 /* Which state array to read or write (all [L][N][N] unless noted). */
 typedef enum {
   MF_ARR_X = 0,        /* X after the last step I (Algorithm 1 returns X) */

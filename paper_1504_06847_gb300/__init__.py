@@ -23,7 +23,8 @@ EXPORTS = ["mf_params_default", "mf_plan_create", "mf_plan_create_f64", "mf_plan
            "mf_plan_device_bytes", "mf_admm_iterate", "mf_admm_iterate_f64", "mf_plan_get_array",
            "mf_plan_set_array", "mf_plan_get_state", "mf_plan_set_state", "mf_plan_get_report",
            "mf_wavelet_filter", "mf_status_string", "mf_plan_set_timing", "mf_plan_get_timing",
-           "mf_kernel_name", "mf_xstep_noalloc", "mf_plan_set_option", "mf_batch_iterate"]
+           "mf_kernel_name", "mf_xstep_noalloc", "mf_plan_set_option", "mf_batch_iterate",
+           "mf_admm_backward"]
 MF_OPT_WAV_TILE = 0
 
 KERNELS = ["rows_fwd", "cols_solve", "rows_inv", "spectral", "wav_ll", "wav_level1", "wav_levelj", "setup",
@@ -104,6 +105,10 @@ def lib():
         L.mf_batch_iterate.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(Params),
                                        ctypes.c_int]
         L.mf_batch_iterate.restype = ctypes.c_int
+        L.mf_admm_backward.argtypes = [vp, vp, ctypes.POINTER(Params), ctypes.c_int, vp, vp,
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]
+        L.mf_admm_backward.restype = ctypes.c_int
         L.mf_plan_set_option.argtypes = [vp, ctypes.c_int, ctypes.c_int]
         L.mf_plan_set_option.restype = ctypes.c_int
         L.mf_xstep_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.POINTER(Params), vp]
@@ -285,6 +290,25 @@ class Plan:
             _check(lib().mf_plan_get_timing(self._h, k, ctypes.byref(ms), ctypes.byref(n)), "mf_plan_get_timing")
             out[name] = (ms.value, n.value)
         return out
+
+    def backward(self, y, n_iter: int, dL_dX, **kw):
+        """Reverse mode of n_iter unrolled iterations (tied rho): returns
+        (dL/dy tensor, dL/dmu_s, dL/dmu_nu, dL/drho) for the cotangent dL_dX of
+        the last X (see mf_admm_backward)."""
+        import torch
+
+        rho = kw.pop("rho", None)
+        if rho is not None:
+            kw.update(rho_P=rho, rho_T=rho, rho_V=rho, rho_S=rho)
+        params = self.params(**kw)
+        y = y.contiguous()
+        g = dL_dX.contiguous()
+        dy = torch.empty_like(y)
+        a, b_, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().mf_admm_backward(self._h, ctypes.c_void_p(y.data_ptr()), ctypes.byref(params), int(n_iter),
+                                      ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(dy.data_ptr()),
+                                      ctypes.byref(a), ctypes.byref(b_), ctypes.byref(c)), "mf_admm_backward")
+        return dy, a.value, b_.value, c.value
 
     def get_state(self):
         import torch

@@ -237,6 +237,8 @@ __global__ void __launch_bounds__(FFT_NT) k_rows_inv(const cx<R>* __restrict__ i
 // ---------------------------------------------------------------------------
 // cols: strip of SW packed columns of one band.
 // ---------------------------------------------------------------------------
+// MODE 3 applies H (X = h B) and MODE 4 applies Q^-1 alone (X = g B): both serve
+// the backward pass.
 // MODE 2 is MODE 1 plus the data-fit partials 1/2 ||y - H x||^2 (Parseval over the
 // half spectrum: interior columns count twice) read from hh/yh.
 template <class R, int N, int MODE>
@@ -300,8 +302,17 @@ __global__ void __launch_bounds__(FFT_NT) k_cols(cx<R>* __restrict__ work, const
         const cx<R> D = csub<R>(Z, Zm);
         const cx<R> B = mk<R>((R)0.5 * D.y, (R)-0.5 * D.x);
         const size_t on = (size_t)band * N + ky;
-        const cx<R> Ax = cadd<R>(cc[o], cscale<R>(A, gg[o]));
-        const cx<R> Bx = cadd<R>(cc_nyq[on], cscale<R>(B, gg_nyq[on]));
+        cx<R> Ax, Bx;
+        if (MODE == 3) {  // H: multiply by the transfer function (1/N^2 of the inverse folded in)
+          Ax = cscale<R>(cmul<R>(hh[o], A), (R)1 / N2);
+          Bx = cscale<R>(cmul<R>(hh_nyq[on], B), (R)1 / N2);
+        } else if (MODE == 4) {  // Q^-1 without the H^T y term
+          Ax = cscale<R>(A, gg[o]);
+          Bx = cscale<R>(B, gg_nyq[on]);
+        } else {
+          Ax = cadd<R>(cc[o], cscale<R>(A, gg[o]));
+          Bx = cadd<R>(cc_nyq[on], cscale<R>(B, gg_nyq[on]));
+        }
         Xh = mk<R>(Ax.x - Bx.y, Ax.y + Bx.x);  // A' + i B'
         if (MODE == 2) {
           const cx<R> ra = csub<R>(yh[o], cscale<R>(cmul<R>(hh[o], Ax), N2));
@@ -309,7 +320,9 @@ __global__ void __launch_bounds__(FFT_NT) k_cols(cx<R>* __restrict__ work, const
           fit += (double)ra.x * ra.x + (double)ra.y * ra.y + (double)rb.x * rb.x + (double)rb.y * rb.y;
         }
       } else {
-        Xh = cadd<R>(cc[o], cscale<R>(Z, gg[o]));
+        if (MODE == 3) Xh = cscale<R>(cmul<R>(hh[o], Z), (R)1 / N2);
+        else if (MODE == 4) Xh = cscale<R>(Z, gg[o]);
+        else Xh = cadd<R>(cc[o], cscale<R>(Z, gg[o]));
         if (MODE == 2) {
           const cx<R> r = csub<R>(yh[o], cscale<R>(cmul<R>(hh[o], Xh), N2));
           fit += 2.0 * ((double)r.x * r.x + (double)r.y * r.y);
@@ -394,6 +407,8 @@ static cudaError_t cols_n(cx<R>* work, int L, const cx<R>* tw, int mode, cx<R>* 
                           const cx<R>* yh, const cx<R>* yhn, double* partials, cudaStream_t s) {
   if (mode == 0) return cols_mode<R, N, 0>(work, L, tw, om, on, cc, ccn, gg, ggn, hh, hhn, yh, yhn, partials, s);
   if (mode == 1) return cols_mode<R, N, 1>(work, L, tw, om, on, cc, ccn, gg, ggn, hh, hhn, yh, yhn, partials, s);
+  if (mode == 3) return cols_mode<R, N, 3>(work, L, tw, om, on, cc, ccn, gg, ggn, hh, hhn, yh, yhn, partials, s);
+  if (mode == 4) return cols_mode<R, N, 4>(work, L, tw, om, on, cc, ccn, gg, ggn, hh, hhn, yh, yhn, partials, s);
   return cols_mode<R, N, 2>(work, L, tw, om, on, cc, ccn, gg, ggn, hh, hhn, yh, yhn, partials, s);
 }
 

@@ -122,7 +122,8 @@ namespace mf {
 template <class R> cudaError_t launch_rows_fwd(const R* in, cx<R>* out, int N, int rows, const cx<R>* tw, cudaStream_t s);
 // Column pass on the packed half spectrum of L bands.  mode 0: forward transform only,
 // unpacked into (out_main, out_nyq).  mode 1: forward, X = c + g B, inverse, in place.
-// mode 2: mode 1 plus the data-fit partials from (hh, yh).
+// mode 2: mode 1 plus the data-fit partials from (hh, yh).  mode 3: X = hh B / N^2 (applies
+// H).  mode 4: X = g B (applies Q^-1 without the H^T y term).
 template <class R> cudaError_t launch_cols(cx<R>* work, int N, int L, const cx<R>* tw, int mode,
                                            cx<R>* out_main, cx<R>* out_nyq,
                                            const cx<R>* cc, const cx<R>* cc_nyq,

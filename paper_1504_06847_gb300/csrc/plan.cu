@@ -575,6 +575,17 @@ cudaError_t launch_shift_psf(const R* psf, R* out, int N, size_t total, cudaStre
 template cudaError_t launch_shift_psf<float>(const float*, float*, int, size_t, cudaStream_t);
 }  // namespace mf
 
+// Entry points for the reverse pass (backward.cu).
+mf_status mf_internal_prepare_f32(mf_plan* p, const float* y, const mf_params* prm, int n_iter, cudaStream_t s,
+                                  WavSet<float>* ws, IterScalars<float>* sc) {
+  return prepare<float>(p, y, prm, n_iter, s, ws, sc);
+}
+cudaError_t mf_internal_iteration_f32(mf_plan* p, const mf_params* prm, const WavSet<float>& ws,
+                                      const IterScalars<float>& sc, cudaStream_t s) {
+  return iteration<float>(p, prm->wavelet_levels, ws.nd, (const WavSet<float>*)p->wset, sc, 0, prm->precision, s);
+}
+void mf_internal_finish(mf_plan* p, const mf_params* prm, int n_iter) { finish(p, prm, n_iter); }
+
 extern "C" {
 
 void mf_params_default(mf_params* p) {

@@ -191,6 +191,183 @@ __global__ void __launch_bounds__(SP_NT) k_spectral(const R* __restrict__ X, R* 
   if (RESID) block_reduce_write<SP_NT>(q, partials + (size_t)blockIdx.x * MF_NQ);
 }
 
+// Adjoint of the spectral step (steps II, IV, V and their duals, and the
+// pointwise part of b) for the tied penalty rho, with the forward recomputed
+// from its inputs (X, old Gamma_P, S^, Gamma_V, Gamma_S^).  In: bb = cotangent
+// of b; cotangents of the outputs Gamma_P', S^', Gamma_V', Gamma_S^' in
+// GPc, Sc, GVc, GSc (overwritten with the cotangents of the old values).
+// Out: Xc = cotangent of X from this step; d mu_nu and d rho partials.
+template <class R, int LP>
+__global__ void __launch_bounds__(SP_NT) k_spectral_bwd(const R* __restrict__ X, const R* __restrict__ GP,
+                                                         const R* __restrict__ Sd, const R* __restrict__ GV,
+                                                         const R* __restrict__ GSd, const R* __restrict__ bb,
+                                                         R* __restrict__ GPc, R* __restrict__ Sc, R* __restrict__ GVc,
+                                                         R* __restrict__ GSc, R* __restrict__ Xc,
+                                                         const R* __restrict__ dctC, int NN, int L, R rho, R mu_nu,
+                                                         double* __restrict__ partials) {
+  constexpr int PT = 4096 / LP;
+  constexpr int TP = PT / 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* C = reinterpret_cast<R*>(smem_raw);
+  R* CT = C + LP * LP;
+  R* T1 = CT + LP * LP;  // X, then the cotangent of X^
+  R* T2 = T1 + LP * PT;  // b_bar
+  const int tid = threadIdx.x;
+  const int tk = tid / TP, tp = tid % TP;
+  const int p0 = blockIdx.x * PT;
+  for (int e = tid; e < LP * LP; e += SP_NT) {
+    const int k = e / LP, l = e % LP;
+    const R v = (k < L && l < L) ? dctC[k * L + l] : (R)0;
+    C[k * LP + l] = v;
+    CT[l * LP + k] = v;
+  }
+  for (int e = tid; e < LP * (PT / 4); e += SP_NT) {
+    const int l = e / (PT / 4), p = 4 * (e % (PT / 4));
+    R v[4] = {0, 0, 0, 0}, w[4] = {0, 0, 0, 0};
+    if (l < L && p0 + p < NN) {
+      V4<R>::ld(X + (size_t)l * NN + p0 + p, v);
+      V4<R>::ld(bb + (size_t)l * NN + p0 + p, w);
+    }
+    V4<R>::st(T1 + l * PT + p, v);
+    V4<R>::st(T2 + l * PT + p, w);
+  }
+  __syncthreads();
+  const int kb = 4 * tk, pb = 4 * tp;
+  const bool pix_ok = p0 + pb < NN;
+  R xr[4][4], br[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    V4<R>::ld(T1 + (kb + a) * PT + pb, xr[a]);
+    V4<R>::ld(T2 + (kb + a) * PT + pb, br[a]);
+  }
+  R xh[4][4] = {}, gh[4][4] = {};
+#pragma unroll 4
+  for (int l = 0; l < LP; l++) {
+    R c4[4], x4[4], b4[4];
+    V4<R>::ld(CT + l * LP + kb, c4);
+    V4<R>::ld(T1 + l * PT + pb, x4);
+    V4<R>::ld(T2 + l * PT + pb, b4);
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        xh[a][c] = fma(c4[a], x4[c], xh[a][c]);
+        gh[a][c] = fma(c4[a], b4[c], gh[a][c]);
+      }
+  }
+  double dmunu = 0.0, drho = 0.0;
+  const R irho = (R)1 / rho, tauv = mu_nu / rho;
+  R xhb[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    const int k = kb + a;
+#pragma unroll
+    for (int c = 0; c < 4; c++) xhb[a][c] = 0;
+    if (k < L && pix_ok) {
+      const size_t o = (size_t)k * NN + p0 + pb;
+      R s[4], gv[4], gs[4], sc_[4], gvc[4], gsc[4];
+      V4<R>::ld(Sd + o, s);
+      V4<R>::ld(GV + o, gv);
+      V4<R>::ld(GSd + o, gs);
+      V4<R>::ld(Sc + o, sc_);
+      V4<R>::ld(GVc + o, gvc);
+      V4<R>::ld(GSc + o, gsc);
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        // forward recomputation
+        const R vt = s[c] - gv[c] * irho;
+        const bool mv = fabs(vt) > tauv;
+        const R sv = vt > 0 ? (R)1 : (vt < 0 ? (R)-1 : (R)0);
+        const R v = mv ? vt - tauv * sv : (R)0;
+        const R sn = (gv[c] + rho * v - gs[c] + rho * xh[a][c]) * ((R)0.5 * irho);
+        // cotangents of the outputs
+        const R A1 = gsc[c] + gh[a][c];         // Gamma_S^'
+        const R A2 = sc_[c] + rho * gh[a][c];   // S^' (outside the duals)
+        const R C1 = gvc[c];                    // Gamma_V'
+        drho += (double)gh[a][c] * sn;
+        const R Sb = A2 - rho * C1 + rho * A1;  // total on S^'
+        R Vb = rho * C1 + (R)0.5 * Sb;
+        drho += (double)C1 * (v - sn) + (double)A1 * (sn - xh[a][c]) +
+                (double)Sb * ((v + xh[a][c]) * ((R)0.5 * irho) - sn * irho);
+        const R vtb = mv ? Vb : (R)0;
+        const R taub = mv ? -sv * Vb : (R)0;
+        dmunu += (double)taub * irho;
+        drho += -(double)taub * mu_nu * irho * irho + (double)vtb * gv[c] * irho * irho;
+        sc_[c] = vtb;
+        gvc[c] = C1 + (R)0.5 * Sb * irho - vtb * irho;
+        gsc[c] = A1 - (R)0.5 * Sb * irho;
+        xhb[a][c] = -rho * A1 + (R)0.5 * Sb;
+      }
+      V4<R>::st(Sc + o, sc_);
+      V4<R>::st(GVc + o, gvc);
+      V4<R>::st(GSc + o, gsc);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 4; a++) V4<R>::st(T1 + (kb + a) * PT + pb, xhb[a]);
+  __syncthreads();
+  R xs[4][4] = {};
+#pragma unroll 4
+  for (int k = 0; k < LP; k++) {
+    R c4[4], u4[4];
+    V4<R>::ld(C + k * LP + kb, c4);
+    V4<R>::ld(T1 + k * PT + pb, u4);
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int c = 0; c < 4; c++) xs[a][c] = fma(c4[a], u4[c], xs[a][c]);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    const int l = kb + a;
+    if (l < L && pix_ok) {
+      const size_t o = (size_t)l * NN + p0 + pb;
+      R gp[4], gpc[4], out[4];
+      V4<R>::ld(GP + o, gp);
+      V4<R>::ld(GPc + o, gpc);
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        const R x = xr[a][c];
+        const R pt = x - gp[c] * irho;
+        const bool mp = pt > 0;
+        const R pp = mp ? pt : (R)0;
+        const R B1 = gpc[c] + br[a][c];  // Gamma_P' (its own cotangent plus b's)
+        const R Pb = rho * br[a][c] + rho * B1;
+        const R ptb = mp ? Pb : (R)0;
+        drho += (double)br[a][c] * pp + (double)B1 * (pp - x) + (double)ptb * gp[c] * irho * irho;
+        out[c] = xs[a][c] + ptb - rho * B1;
+        gpc[c] = B1 - ptb * irho;
+      }
+      V4<R>::st(GPc + o, gpc);
+      V4<R>::st(Xc + o, out);
+    }
+  }
+  double q[Q_COUNT];
+#pragma unroll
+  for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
+  q[Q_XMIN] = 1e300;
+  q[1] = dmunu;
+  q[2] = drho;
+  block_reduce_write<SP_NT>(q, partials + (size_t)blockIdx.x * MF_NQ);
+}
+
+template <class R, int LP>
+static cudaError_t spectral_bwd_lp(const R* X, const R* GP, const R* Sd, const R* GV, const R* GSd, const R* bb,
+                                   R* GPc, R* Sc, R* GVc, R* GSc, R* Xc, const R* dctC, int N, int L, R rho,
+                                   R mu_nu, double* partials, int* nblocks, cudaStream_t s) {
+  constexpr int PT = 4096 / LP;
+  const int NN = N * N;
+  const int blocks = (NN + PT - 1) / PT;
+  *nblocks = blocks;
+  const size_t sm = sizeof(R) * (2 * LP * LP + 2 * LP * PT);
+  cudaError_t e = cudaFuncSetAttribute(k_spectral_bwd<R, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_spectral_bwd<R, LP><<<blocks, SP_NT, sm, s>>>(X, GP, Sd, GV, GSd, bb, GPc, Sc, GVc, GSc, Xc, dctC, NN, L, rho,
+                                                  mu_nu, partials);
+  return cudaGetLastError();
+}
+
 template <class R, int LP>
 static cudaError_t spectral_lp(const R* X, R* GP, R* Sd, R* GV, R* GSd, R* b, const R* dctC, int N, int L,
                                IterScalars<R> sc, double* partials, int resid, cudaStream_t s) {
@@ -237,6 +414,26 @@ cudaError_t launch_spectral(const R* X, R* GP, R* Sd, R* GV, R* GSd, R* b, const
     default: return cudaErrorInvalidValue;
   }
 }
+
+template <class R>
+cudaError_t launch_spectral_bwd(const R* X, const R* GP, const R* Sd, const R* GV, const R* GSd, const R* bb, R* GPc,
+                                R* Sc, R* GVc, R* GSc, R* Xc, const R* dctC, int N, int L, R rho, R mu_nu,
+                                double* partials, int* nblocks, cudaStream_t s) {
+  switch (padded_L(L)) {
+    case 8: return spectral_bwd_lp<R, 8>(X, GP, Sd, GV, GSd, bb, GPc, Sc, GVc, GSc, Xc, dctC, N, L, rho, mu_nu,
+                                         partials, nblocks, s);
+    case 16: return spectral_bwd_lp<R, 16>(X, GP, Sd, GV, GSd, bb, GPc, Sc, GVc, GSc, Xc, dctC, N, L, rho, mu_nu,
+                                           partials, nblocks, s);
+    case 32: return spectral_bwd_lp<R, 32>(X, GP, Sd, GV, GSd, bb, GPc, Sc, GVc, GSc, Xc, dctC, N, L, rho, mu_nu,
+                                           partials, nblocks, s);
+    case 64: return spectral_bwd_lp<R, 64>(X, GP, Sd, GV, GSd, bb, GPc, Sc, GVc, GSc, Xc, dctC, N, L, rho, mu_nu,
+                                           partials, nblocks, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t launch_spectral_bwd<float>(const float*, const float*, const float*, const float*,
+                                                const float*, const float*, float*, float*, float*, float*, float*,
+                                                const float*, int, int, float, float, double*, int*, cudaStream_t);
 
 template cudaError_t launch_spectral<float>(const float*, float*, float*, float*, float*, float*, const float*, int,
                                             int, IterScalars<float>, double*, int, cudaStream_t);

@@ -811,6 +811,180 @@ __global__ void __launch_bounds__(WNT) k_wav_ll(const R* __restrict__ in_img, si
 }
 
 // ---------------------------------------------------------------------------
+// Reverse mode (unrolled iterations): plain periodic level transforms on full
+// coefficient arrays, one thread per output, and the adjoint of the
+// threshold / dual step.  Taps come from the constant tables with a runtime K.
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void k_ana_rows(const R* __restrict__ src, int sp, size_t ss, R* __restrict__ tmp, int M, int K,
+                           int nimg) {
+  const size_t total = (size_t)nimg * M * (M / 2);
+  const int F = 2 * K;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % (M / 2));
+    const int r = (int)((e / (M / 2)) % M);
+    const size_t img = e / ((size_t)M * (M / 2));
+    const R* row = src + img * ss + (size_t)r * sp;
+    R a = 0, d = 0;
+    for (int n = 0; n < F; n++) {
+      const R v = row[(2 * i + n) & (M - 1)];
+      a = fma(Taps<R>::h(K, n), v, a);
+      d = fma(Taps<R>::g(K, n), v, d);
+    }
+    R* t = tmp + img * (size_t)M * M + (size_t)r * M;
+    t[i] = a;
+    t[M / 2 + i] = d;
+  }
+}
+
+template <class R>
+__global__ void k_ana_cols(const R* __restrict__ tmp, int M, int K, int nimg, R* __restrict__ dst, int dp,
+                           size_t ds) {
+  const size_t total = (size_t)nimg * (M / 2) * M;
+  const int F = 2 * K;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % M);
+    const int i = (int)((e / M) % (M / 2));
+    const size_t img = e / ((size_t)M * (M / 2));
+    const R* t = tmp + img * (size_t)M * M + c;
+    R a = 0, d = 0;
+    for (int n = 0; n < F; n++) {
+      const R v = t[(size_t)((2 * i + n) & (M - 1)) * M];
+      a = fma(Taps<R>::h(K, n), v, a);
+      d = fma(Taps<R>::g(K, n), v, d);
+    }
+    R* o = dst + img * ds + c;
+    o[(size_t)i * dp] = a;
+    o[(size_t)(M / 2 + i) * dp] = d;
+  }
+}
+
+template <class R>
+__global__ void k_syn_cols(const R* __restrict__ src, int sp, size_t ss, R* __restrict__ tmp, int M, int K,
+                           int nimg) {
+  const size_t total = (size_t)nimg * M * M;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % M);
+    const int m = (int)((e / M) % M);
+    const size_t img = e / ((size_t)M * M);
+    const R* col = src + img * ss + c;
+    R v = 0;
+    for (int n = (m & 1); n < 2 * K; n += 2) {
+      const int i = ((m - n) >> 1) & (M / 2 - 1);
+      v = fma(Taps<R>::h(K, n), col[(size_t)i * sp], v);
+      v = fma(Taps<R>::g(K, n), col[(size_t)(M / 2 + i) * sp], v);
+    }
+    tmp[img * (size_t)M * M + (size_t)m * M + c] = v;
+  }
+}
+
+template <class R>
+__global__ void k_syn_rows(const R* __restrict__ tmp, int M, int K, int nimg, R* __restrict__ dst, int dp,
+                           size_t ds, int accumulate) {
+  const size_t total = (size_t)nimg * M * M;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(e % M);
+    const int m = (int)((e / M) % M);
+    const size_t img = e / ((size_t)M * M);
+    const R* row = tmp + img * (size_t)M * M + (size_t)m * M;
+    R v = 0;
+    for (int n = (x & 1); n < 2 * K; n += 2) {
+      const int i = ((x - n) >> 1) & (M / 2 - 1);
+      v = fma(Taps<R>::h(K, n), row[i], v);
+      v = fma(Taps<R>::g(K, n), row[M / 2 + i], v);
+    }
+    R* o = dst + img * ds + (size_t)m * dp + x;
+    *o = accumulate ? *o + v : v;
+  }
+}
+
+// Adjoint of step III and its dual update for one coefficient, with the
+// forward recomputed from z = (W_k X) and the old multiplier gam:
+//   T~ = z - gam/rho, T = S_tau(T~), tau = mu_s/rho,
+//   Gamma_T' = gam + rho (T - z),  U = Gamma_T' + rho T.
+// In: g1 = cotangent of Gamma_T', ub = cotangent of U (= w_k W_k b_bar).
+// Out: cotangent of z (into zc) and of gam (into gc); d mu_s and d rho partials.
+template <class R>
+__global__ void k_wav_bwd_point(R* __restrict__ zc, const R* __restrict__ uc, const R* __restrict__ gam_old,
+                                R* __restrict__ gc, size_t per_basis, int nd, const WavSet<R>* __restrict__ ws,
+                                R rho, R mu_s, double* __restrict__ partials) {
+  const size_t total = per_basis * nd;
+  double dmu = 0.0, drho = 0.0;
+  const R tau = mu_s / rho;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / per_basis);
+    const R w = ws->w[k];
+    const R z = zc[e], gam = gam_old[e], g1 = gc[e], ub = w * uc[e];
+    const R tt = z - gam / rho;
+    const bool m = fabs(tt) > tau;
+    const R sg = tt > 0 ? (R)1 : (tt < 0 ? (R)-1 : (R)0);
+    const R t = m ? tt - tau * sg : (R)0;
+    const R tb = rho * g1 + 2 * rho * ub;
+    const R ttb = m ? tb : (R)0;
+    const R taub = m ? -sg * tb : (R)0;
+    zc[e] = -rho * g1 - rho * ub + ttb;
+    gc[e] = g1 + ub - ttb / rho;
+    dmu += (double)taub / rho;
+    drho += (double)g1 * (t - z) + (double)ub * (2 * t - z) - (double)taub * mu_s / (rho * rho) +
+            (double)ttb * gam / (rho * rho);
+  }
+  double q[Q_COUNT];
+#pragma unroll
+  for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
+  q[Q_XMIN] = 1e300;
+  q[0] = dmu;
+  q[2] = drho;
+  block_reduce_write<WNT>(q, partials + (size_t)blockIdx.x * MF_NQ);
+}
+
+static unsigned simple_grid(size_t total) {
+  size_t b = (total + WNT - 1) / WNT;
+  return (unsigned)(b < 152 * 32 ? (b ? b : 1) : 152 * 32);
+}
+
+template <class R>
+cudaError_t launch_wav_analysis_full(const R* src, R* coef, R* tmp, int N, int L, int J, int nd,
+                                     const int* Ks, cudaStream_t s) {
+  const size_t NN = (size_t)N * N;
+  for (int k = 0; k < nd; k++) {
+    R* ck = coef + (size_t)k * L * NN;
+    for (int j = 1; j <= J; j++) {
+      const int M = N >> (j - 1);
+      const R* in = j == 1 ? src : ck;
+      k_ana_rows<R><<<simple_grid((size_t)L * M * (M / 2)), WNT, 0, s>>>(in, N, NN, tmp, M, Ks[k], L);
+      k_ana_cols<R><<<simple_grid((size_t)L * M * (M / 2)), WNT, 0, s>>>(tmp, M, Ks[k], L, ck, N, NN);
+    }
+  }
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_wav_synthesis_acc(R* coef, R* out, R* tmp, int N, int L, int J, int nd, const int* Ks,
+                                     cudaStream_t s) {
+  const size_t NN = (size_t)N * N;
+  for (int k = 0; k < nd; k++) {
+    R* ck = coef + (size_t)k * L * NN;
+    for (int j = J; j >= 1; j--) {
+      const int M = N >> (j - 1);
+      k_syn_cols<R><<<simple_grid((size_t)L * M * M), WNT, 0, s>>>(ck, N, NN, tmp, M, Ks[k], L);
+      if (j == 1) k_syn_rows<R><<<simple_grid((size_t)L * M * M), WNT, 0, s>>>(tmp, M, Ks[k], L, out, N, NN, 1);
+      else k_syn_rows<R><<<simple_grid((size_t)L * M * M), WNT, 0, s>>>(tmp, M, Ks[k], L, ck, N, NN, 0);
+    }
+  }
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_wav_bwd_point(R* zc, const R* uc, const R* gam_old, R* gc, size_t per_basis, int nd,
+                                 const WavSet<R>* ws, R rho, R mu_s, double* partials, int* nblocks,
+                                 cudaStream_t s) {
+  const unsigned g = simple_grid(per_basis * nd);
+  *nblocks = (int)g;
+  k_wav_bwd_point<R><<<g, WNT, 0, s>>>(zc, uc, gam_old, gc, per_basis, nd, ws, rho, mu_s, partials);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 // Output tile edge of the fused level kernels: the largest of the allowed
@@ -910,5 +1084,12 @@ cudaError_t launch_wav_level(const R* in, size_t, size_t, const R* rcoarse, R* o
 INST(float)
 INST(double)
 #undef INST
+
+template cudaError_t launch_wav_analysis_full<float>(const float*, float*, float*, int, int, int, int, const int*,
+                                                     cudaStream_t);
+template cudaError_t launch_wav_synthesis_acc<float>(float*, float*, float*, int, int, int, int, const int*,
+                                                     cudaStream_t);
+template cudaError_t launch_wav_bwd_point<float>(float*, const float*, const float*, float*, size_t, int,
+                                                 const WavSet<float>*, float, float, double*, int*, cudaStream_t);
 
 }  // namespace mf

@@ -1,0 +1,105 @@
+"""Differentiable form: the CUDA reverse pass against the FP64 reference
+gradients (torch restatement, itself pinned to finite differences of the C
+oracle) and against central finite differences of the C oracle directly.
+
+Tolerance: 1e-3 relative, |g_gpu - g_ref| / max(|g_ref|, 1), for the
+scalars; dL/dy is checked through its directional derivatives along three
+seeded unit directions (within 1e-3 of ||dL/dy||) and its relative L2 error
+(within 1e-2).  The forward runs in FP32, so a coefficient within FP32
+rounding of a threshold may take the other branch than in the FP64 run; such
+a flip changes dL/dy locally, which an elementwise bound would misread.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import paper_1504_06847_gb300 as mf  # noqa: E402
+from oracle import torch_ref  # noqa: E402
+from paper_1504_06847_gb300 import autograd, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    yield
+
+
+def _gpu_grads(c, K, J, mu_s=0.05, mu_nu=0.01, rho=1.0):
+    plan = mf.Plan(torch.tensor(c.psf, dtype=torch.float32, device="cuda"))
+    y = torch.tensor(c.y, dtype=torch.float32, device="cuda")
+    plan.iterate(y, K, wavelet_levels=J, mu_s=mu_s, mu_nu=mu_nu, rho_P=rho, rho_T=rho, rho_V=rho, rho_S=rho)
+    x = plan.x()
+    gx = 2 * (x - torch.tensor(c.sky, dtype=torch.float32, device="cuda"))
+    dy, dms, dmn, dr = plan.backward(y, K, gx, wavelet_levels=J, mu_s=mu_s, mu_nu=mu_nu, rho=rho)
+    return dy.double().cpu().numpy(), dms, dmn, dr
+
+
+@pytest.mark.parametrize("N,L,K,J", [(32, 4, 6, 2), (64, 8, 20, 3)])
+def test_backward_matches_fp64_reference(N, L, K, J):
+    c = synth.make_cube(N, L, n_sources=3 + N // 16, n_antennas=32, seed=17 + N)
+    ref = torch_ref.loss_and_grads(c.psf, c.y, c.sky, 0.05, 0.01, 1.0, K, J=J)
+    dy, dms, dmn, dr = _gpu_grads(c, K, J)
+    for g, r in ((dms, ref[2]), (dmn, ref[3]), (dr, ref[4])):
+        assert abs(g - r) <= 1e-3 * max(abs(r), 1.0), (g, r, ref[2:5])
+    rn = np.linalg.norm(ref[1])
+    assert np.linalg.norm(dy - ref[1]) <= 1e-2 * rn
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        d = rng.normal(size=dy.shape)
+        d /= np.linalg.norm(d)
+        assert abs(np.sum(d * (dy - ref[1]))) <= 1e-3 * rn
+
+
+def test_autograd_function_agrees_with_plan_backward():
+    c = synth.make_cube(32, 4, n_sources=4, n_antennas=32, seed=5)
+    plan = mf.Plan(torch.tensor(c.psf, dtype=torch.float32, device="cuda"))
+    y = torch.tensor(c.y, dtype=torch.float32, device="cuda", requires_grad=True)
+    ms = torch.tensor(0.05, dtype=torch.float64, requires_grad=True)
+    mn = torch.tensor(0.01, dtype=torch.float64, requires_grad=True)
+    rh = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    x = autograd.unrolled(plan, y, ms, mn, rh, n_iter=6, wavelet_levels=2)
+    loss = ((x - torch.tensor(c.sky, dtype=torch.float32, device="cuda")) ** 2).sum()
+    loss.backward()
+    dy, dms, dmn, dr = _gpu_grads(c, 6, 2)
+    assert np.allclose(y.grad.double().cpu().numpy(), dy, rtol=0, atol=1e-6 * np.abs(dy).max())
+    assert abs(ms.grad.item() - dms) <= 1e-9 * max(1.0, abs(dms))
+    assert abs(rh.grad.item() - dr) <= 1e-9 * max(1.0, abs(dr))
+
+
+def test_scalar_gradients_match_oracle_finite_differences_256x256x32():
+    # the differentiable-form workload: 256 x 256 x 32, 20 unrolled iterations
+    c = synth.workload("256x256x32")
+    K, J = 20, 3
+    dy, dms, dmn, dr = _gpu_grads(c, K, J)
+
+    def loss(mu_s, mu_nu, rho):
+        prm = dict(mu_eps=0.001, mu_s=mu_s, mu_nu=mu_nu, rho_P=rho, rho_T=rho, rho_V=rho, rho_S=rho)
+        st, _ = oracle.Problem(c.psf, c.y, prm, J=J).run(K)
+        return float(((st["X"] - c.sky) ** 2).sum())
+
+    h = 1e-4
+    for i, (g, base) in enumerate(((dms, 0.05), (dmn, 0.01), (dr, 1.0))):
+        args_p = [0.05, 0.01, 1.0]
+        args_m = [0.05, 0.01, 1.0]
+        args_p[i] = base + h
+        args_m[i] = base - h
+        fd = (loss(*args_p) - loss(*args_m)) / (2 * h)
+        assert abs(g - fd) <= 1e-3 * max(abs(fd), 1.0), (i, g, fd)
+
+
+def test_backward_rejects_untied_penalties():
+    c = synth.make_cube(32, 4, n_sources=2, n_antennas=16, seed=1)
+    plan = mf.Plan(torch.tensor(c.psf, dtype=torch.float32, device="cuda"))
+    y = torch.tensor(c.y, dtype=torch.float32, device="cuda")
+    with pytest.raises(mf.MFError) as e:
+        plan.backward(y, 3, torch.zeros_like(y), rho_P=1.0, rho_T=2.0, rho_V=1.0, rho_S=1.0)
+    assert e.value.status == mf.MF_ERR_INVALID
