@@ -6,8 +6,9 @@
 // accumulated in FP32 in tensor memory (the a_lo b_lo term, ~2^-16 relative,
 // is dropped).
 //
-// One CTA = 128 pixels = the M dimension of the MMA, so after tcgen05.ld each
-// thread holds one pixel's whole spectrum for the pointwise updates.
+// One CTA = 128 pixels = the M dimension of the MMA; after tcgen05.ld each
+// thread holds half of one pixel's spectrum for the pointwise updates (warps
+// w and w + 4 read the same tensor-memory lanes).
 // Operand layout in shared memory: no swizzle, K-major core matrices of
 // 8 rows x 16 bytes; element (r, k) of an R x K operand sits at byte
 // (r / 8) SBO + (k / 8) LBO + (r % 8) 16 + (k % 8) 2 with LBO = 128 and
@@ -28,7 +29,7 @@ namespace mf {
 namespace {
 
 constexpr int TC_M = 128;       // pixels per CTA (MMA M)
-constexpr int TC_NT = 128;      // threads per CTA
+constexpr int TC_NT = 256;      // threads per CTA: two per pixel, each on half of the spectral axis
 constexpr int TC_TMEM_COLS = 64;
 constexpr long long TC_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
@@ -149,7 +150,7 @@ __device__ __forceinline__ uint32_t seg_off(int r, int k0) {
 }
 
 template <int LP, int RESID>
-__global__ void __launch_bounds__(TC_NT, 1) k_spectral_tc(const float* __restrict__ X, float* __restrict__ GP,
+__global__ void __launch_bounds__(TC_NT, 2) k_spectral_tc(const float* __restrict__ X, float* __restrict__ GP,
                                                            float* __restrict__ Sd, float* __restrict__ GV,
                                                            float* __restrict__ GSd, float* __restrict__ b,
                                                            const uint16_t* __restrict__ bmats, int NN, int L,
@@ -167,7 +168,10 @@ __global__ void __launch_bounds__(TC_NT, 1) k_spectral_tc(const float* __restric
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int p = blockIdx.x * TC_M + tid;
+  const int row = tid & (TC_M - 1);     // pixel within the tile = tensor-memory lane
+  const int half = tid / TC_M;          // which half of the bands / frequencies
+  constexpr int HL = LP / 2;            // bands or frequencies per thread (a multiple of 8)
+  const int p = blockIdx.x * TC_M + row;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -183,27 +187,31 @@ __global__ void __launch_bounds__(TC_NT, 1) k_spectral_tc(const float* __restric
     uint4* dst = reinterpret_cast<uint4*>(B1hi);
     for (int e = tid; e < 4 * LP * LP / 8; e += TC_NT) dst[e] = src[e];
   }
-  // this pixel's spectrum: FP32 copy and the split A operand
+  // this pixel's half spectrum: FP32 copy and the split A operand
+  {
+    float v[HL];
 #pragma unroll
-  for (int l0 = 0; l0 < LP; l0 += 8) {
-    float v[8];
-#pragma unroll
-    for (int t = 0; t < 8; t++) {
-      const int l = l0 + t;
+    for (int t = 0; t < HL; t++) {
+      const int l = half * HL + t;
       v[t] = l < L ? X[(size_t)l * NN + p] : 0.f;
-      Xs[l * TC_M + tid] = v[t];
     }
-    uint4 hi, lo;
-    split8(v, hi, lo);
-    *reinterpret_cast<uint4*>(reinterpret_cast<char*>(Ahi) + seg_off<LP>(tid, l0)) = hi;
-    *reinterpret_cast<uint4*>(reinterpret_cast<char*>(Alo) + seg_off<LP>(tid, l0)) = lo;
+#pragma unroll
+    for (int c0 = 0; c0 < HL; c0 += 8) {
+      const int l0 = half * HL + c0;
+#pragma unroll
+      for (int t = 0; t < 8; t++) Xs[(l0 + t) * TC_M + row] = v[c0 + t];
+      uint4 hi, lo;
+      split8(v + c0, hi, lo);
+      *reinterpret_cast<uint4*>(reinterpret_cast<char*>(Ahi) + seg_off<LP>(row, l0)) = hi;
+      *reinterpret_cast<uint4*>(reinterpret_cast<char*>(Alo) + seg_off<LP>(row, l0)) = lo;
+    }
   }
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+  const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
 
   // x^ = X W_nu
   if (tid == 0) {
@@ -222,8 +230,8 @@ __global__ void __launch_bounds__(TC_NT, 1) k_spectral_tc(const float* __restric
 
   if (ok) {
     // DCT-domain part of steps IV, V, VI; U = Gamma_S + rho_S S becomes the next A operand
-#pragma unroll 1
-    for (int k0 = 0; k0 < LP; k0 += 8) {
+#pragma unroll
+    for (int k0 = half * HL; k0 < (half + 1) * HL; k0 += 8) {
       float xh[8], u[8];
       tmem_ld8(trow + k0, xh);
 #pragma unroll
@@ -252,8 +260,8 @@ __global__ void __launch_bounds__(TC_NT, 1) k_spectral_tc(const float* __restric
       }
       uint4 hi, lo;
       split8(u, hi, lo);
-      *reinterpret_cast<uint4*>(reinterpret_cast<char*>(Ahi) + seg_off<LP>(tid, k0)) = hi;
-      *reinterpret_cast<uint4*>(reinterpret_cast<char*>(Alo) + seg_off<LP>(tid, k0)) = lo;
+      *reinterpret_cast<uint4*>(reinterpret_cast<char*>(Ahi) + seg_off<LP>(row, k0)) = hi;
+      *reinterpret_cast<uint4*>(reinterpret_cast<char*>(Alo) + seg_off<LP>(row, k0)) = lo;
     }
   }
   fence_async_smem();
@@ -271,8 +279,8 @@ __global__ void __launch_bounds__(TC_NT, 1) k_spectral_tc(const float* __restric
 
   if (ok) {
     // pixel domain: step II, Gamma_P, and b
-#pragma unroll 1
-    for (int l0 = 0; l0 < LP; l0 += 8) {
+#pragma unroll
+    for (int l0 = half * HL; l0 < (half + 1) * HL; l0 += 8) {
       float bs[8];
       tmem_ld8(trow + l0, bs);
 #pragma unroll
@@ -280,7 +288,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_spectral_tc(const float* __restric
         const int l = l0 + t;
         if (l < L) {
           const size_t o = (size_t)l * NN + p;
-          const float x = Xs[l * TC_M + tid];
+          const float x = Xs[l * TC_M + row];
           const float gp = GP[o];
           const float pt = x - gp * sc.inv_rho_P;
           const float pp = pt > 0.f ? pt : 0.f;
