@@ -539,37 +539,41 @@ __device__ __forceinline__ void level_tile_t(const R* in, int off, R* ra, R* rd,
     }
   }
   __syncthreads();
-  // 5. row synthesis: output row m, columns OPI j..OPI j+OPI-1 (runs of RB);
+  // 5. row synthesis: output row m, columns OPI j..OPI j+OPI-1 (runs of RS);
   //    consecutive threads take consecutive rows
+  {
+    constexpr int RS = OPI < RB ? OPI : RB;
+    constexpr int NS = RS / 2 + K - 1;
 #pragma unroll
-  for (int s = 0; s < C::IPT; s++) {
-    const int it = tid + s * WNT;
-    const int m = it % T, j = it / T;
-    R out[OPI];
+    for (int s = 0; s < C::IPT; s++) {
+      const int it = tid + s * WNT;
+      const int m = it % T, j = it / T;
+      R out[OPI];
 #pragma unroll
-    for (int hh = 0; hh < OPI / RB; hh++) {
-      const R* cl = ra + m * B_CP + (OPI / 2) * j + (RB / 2) * hh;
-      const R* ch = rd + m * B_CP + (OPI / 2) * j + (RB / 2) * hh;
-      R ua[NU], ud[NU];
+      for (int hh = 0; hh < OPI / RS; hh++) {
+        const R* cl = ra + m * B_CP + (OPI / 2) * j + (RS / 2) * hh;
+        const R* ch = rd + m * B_CP + (OPI / 2) * j + (RS / 2) * hh;
+        R ua[NS], ud[NS];
 #pragma unroll
-      for (int ii = 0; ii < NU; ii++) {
-        ua[ii] = cl[ii];
-        ud[ii] = ch[ii];
-      }
-#pragma unroll
-      for (int t = 0; t < RB; t++) {
-        const int par = t & 1;
-        R acc = 0;
-#pragma unroll
-        for (int n2 = 0; n2 < K; n2++) {
-          const int n = 2 * n2 + par;
-          const int ii = (t - par) / 2 - n2 + K - 1;
-          acc = fma(hr(n), ua[ii], fma(gr(n), ud[ii], acc));
+        for (int ii = 0; ii < NS; ii++) {
+          ua[ii] = cl[ii];
+          ud[ii] = ch[ii];
         }
-        out[RB * hh + t] = acc;
+#pragma unroll
+        for (int t = 0; t < RS; t++) {
+          const int par = t & 1;
+          R acc = 0;
+#pragma unroll
+          for (int n2 = 0; n2 < K; n2++) {
+            const int n = 2 * n2 + par;
+            const int ii = (t - par) / 2 - n2 + K - 1;
+            acc = fma(hr(n), ua[ii], fma(gr(n), ud[ii], acc));
+          }
+          out[RS * hh + t] = acc;
+        }
       }
+      emit(s, m, OPI * j, out);
     }
-    emit(s, m, OPI * j, out);
   }
 #undef hr
 #undef gr
@@ -673,6 +677,35 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_level1_t(const R* __re
   if (RESID) block_reduce_write<WNT>(q, partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * MF_NQ);
 }
 
+// One basis of a coarser level on a T x T tile: loads its input tile and writes
+// the level's synthesis into R_{j-1}.  Not inlined (see level1_basis).
+template <class R, int T, int K, int RESID>
+__device__ __noinline__ void levelj_basis(const R* __restrict__ src, R* in, R* ra, R* rd, R* sb, R* __restrict__ dst,
+                                          int M, int y0, int x0, const R* __restrict__ gto, R* __restrict__ gtn,
+                                          int N, const R* __restrict__ rco, IterScalars<R> sc, R w, double* q) {
+  auto emit = [&](int, int m, int x, const R* v) {
+    R* o = dst + (size_t)(y0 + m) * M + x0 + x;
+#pragma unroll
+    for (int t = 0; t < TC<T>::OPI; t++) o[t] = v[t];
+  };
+  load_tile_t<R, T>(src, M, y0 - 2 * K + 2, x0 - 2 * K + 2, T + 4 * K - 4, in);
+  __syncthreads();
+  level_tile_t<R, T, K, RESID>(in, 0, ra, rd, sb, nullptr, nullptr, M, y0, x0, gto, gtn, N, rco, sc, w, q, emit);
+}
+
+// L2 prefetch of a basis's input tile at a coarser level.
+template <class R, int T>
+__device__ __forceinline__ void prefetch_tile(const R* src, int M, int K, int y0, int x0) {
+  const int H = T + 4 * K - 4, r0 = y0 - 2 * K + 2, c0 = x0 - 2 * K + 2;
+  const int chunks = (H + 31) / 32;
+  for (int e = threadIdx.x; e < H * chunks; e += WNT) {
+    const int r = e / chunks, ch = e % chunks;
+    prefetch_l2(src + (size_t)((r0 + r) & (M - 1)) * M + ((c0 + 32 * ch) & (M - 1)));
+  }
+}
+
+// Coarser level j >= 2 (M = N / 2^(j-1)): every basis in one CTA, in turn, with
+// the next basis's tile and coefficients prefetched into L2; writes R_{j-1}.
 template <class R, int T, int RESID>
 __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_levelj_t(const R* __restrict__ in_img,
                                                                   R* __restrict__ out_img,
@@ -684,33 +717,32 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_levelj_t(const R* __re
   R *ra, *rd, *sb;
   R* in = tile_smem<R, T>(ra, rd, sb);
   const int tpd = M / T;
-  const int band = blockIdx.y, k = blockIdx.z;
+  const int band = blockIdx.y;
   const int y0 = (blockIdx.x / tpd) * T, x0 = (blockIdx.x % tpd) * T;
-  const size_t MM = (size_t)M * M;
-  const R* src = in_img + ((size_t)k * L + band) * MM;
-  R* dst = out_img + ((size_t)k * L + band) * MM;
-  const size_t gofs = ((size_t)k * L + band) * (size_t)N * N;
-  const R* rc = coarsest ? nullptr : rco + ((size_t)k * L + band) * (MM / 4);
+  const size_t MM = (size_t)M * M, NN = (size_t)N * N;
   double q[Q_COUNT];
 #pragma unroll
   for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
   q[Q_XMIN] = 1e300;
-  const R w = ws->w[k];
-  auto emit = [&](int, int m, int x, const R* v) {
-    R* o = dst + (size_t)(y0 + m) * M + x0 + x;
-#pragma unroll
-    for (int t = 0; t < TC<T>::OPI; t++) o[t] = v[t];
-  };
-  prefetch_level<R, T>(ws->K[k], gto + gofs, rc, M, N, y0, x0);
-  MF_K_SWITCH(ws->K[k], {
-    load_tile_t<R, T>(src, M, y0 - 2 * KK + 2, x0 - 2 * KK + 2, T + 4 * KK - 4, in);
+  const int nd = ws->nd;
+  auto src_of = [&](int k) { return in_img + ((size_t)k * L + band) * MM; };
+  auto rc_of = [&](int k) { return coarsest ? (const R*)nullptr : rco + ((size_t)k * L + band) * (MM / 4); };
+  if (nd > 0) {
+    prefetch_tile<R, T>(src_of(0), M, ws->K[0], y0, x0);
+    prefetch_level<R, T>(ws->K[0], gto + (size_t)band * NN, rc_of(0), M, N, y0, x0);
+  }
+  for (int k = 0; k < nd; k++) {
+    if (k + 1 < nd) {
+      prefetch_tile<R, T>(src_of(k + 1), M, ws->K[k + 1], y0, x0);
+      prefetch_level<R, T>(ws->K[k + 1], gto + ((size_t)(k + 1) * L + band) * NN, rc_of(k + 1), M, N, y0, x0);
+    }
+    const size_t gofs = ((size_t)k * L + band) * NN;
+    R* dst = out_img + ((size_t)k * L + band) * MM;
+    MF_K_SWITCH(ws->K[k], (levelj_basis<R, T, KK, RESID>(src_of(k), in, ra, rd, sb, dst, M, y0, x0, gto + gofs,
+                                                         gtn + gofs, N, rc_of(k), sc, ws->w[k], q)));
     __syncthreads();
-    level_tile_t<R, T, KK, RESID>(in, 0, ra, rd, sb, nullptr, nullptr, M, y0, x0, gto + gofs, gtn + gofs, N, rc,
-                                  sc, w, q, emit);
-  });
-  if (RESID)
-    block_reduce_write<WNT>(
-        q, partials + (((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * MF_NQ);
+  }
+  if (RESID) block_reduce_write<WNT>(q, partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * MF_NQ);
 }
 
 // Low-low analysis: LL_j (M/2 x M/2) of the M x M input, for one basis per CTA
@@ -999,7 +1031,7 @@ template <class R>
 int wav_level_blocks(int M, int L, int nd, int pref) {
   const int T = level_tile_edge(M, pref);
   const int tiles = (M / T) * (M / T);
-  return tiles * L * nd;
+  return T >= 32 ? tiles * L : tiles * L * nd;  // the T = 64 / 32 kernels loop over bases in a CTA
 }
 
 template <class R>
@@ -1038,7 +1070,7 @@ static cudaError_t launch_level_t(const R* in, const R* rcoarse, R* out, const R
     return launch_k<R>(k_wav_level1_t<R, T, 0>, grid, sm1, s, in, out, gt_old, gt_new, rcoarse, N, L, coarsest, ws,
                        sc, partials);
   }
-  dim3 grid(tiles, L, nd);
+  dim3 grid(tiles, L);
   const size_t sm = sizeof(R) * TC<T>::SMEM;
   if (resid)
     return launch_k<R>(k_wav_levelj_t<R, T, 1>, grid, sm, s, in, out, gt_old, gt_new, rcoarse, N, M, L, coarsest, ws,
