@@ -8,7 +8,7 @@
 #include <cstddef>
 #include <vector>
 
-#include "../../include/mf.h"
+#include "mf.h"
 
 #define MF_MAX_K 8        // DbK with K <= 8 (Db1..Db8 of the paper's dictionary)
 #define MF_MAX_F 16       // 2 * MF_MAX_K taps
