@@ -21,6 +21,8 @@
 // neighbouring tile writes new ones.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "mf_internal.cuh"
 #include "reduce.cuh"
 
@@ -399,115 +401,71 @@ __device__ __forceinline__ void level_tile_t(const R* in, int off, R* ra, R* rd,
     }
   }
   __syncthreads();
-  // 2. column analysis: column c of ra (sel 0) or rd (sel 1), coefficient rows RB j..
-  for (int it = tid; it < 2 * CW * NRUN; it += WNT) {
-    const int c = it % CW, rest = it / CW;
-    const int j = rest % NRUN, sel = rest / NRUN;
-    const R* col = (sel ? rd : ra) + 2 * RB * j * B_CP + c;
-    R v[NV];
-#pragma unroll
-    for (int t = 0; t < NV; t++) v[t] = col[t * B_CP];
-    R* dlo = sb + (sel ? 1 : 0) * SBQ + RB * j * B_CP + c;  // top-left / top-right
-    R* dhi = sb + (sel ? 3 : 2) * SBQ + RB * j * B_CP + c;  // bottom-left / bottom-right
-#pragma unroll
-    for (int i = 0; i < RB; i++) {
-      R lo = 0, hi = 0;
-#pragma unroll
-      for (int n = 0; n < F; n++) {
-        lo = fma(hr(n), v[2 * i + n], lo);
-        hi = fma(gr(n), v[2 * i + n], hi);
-      }
-      dlo[i * B_CP] = lo;
-      dhi[i * B_CP] = hi;
-    }
-  }
-  __syncthreads();
-  // 3. threshold and dual update of this level's coefficients.  Offsets are
-  //    32-bit within the band image; each thread issues its global loads
-  //    (old Gamma_T, or the coarse reconstruction for the low-low band)
-  //    before using them.
+  // 2. column analysis of column c of ra (sel 0) or rd (sel 1) into
+  //    coefficient rows RB j..RB j+RB-1 of the low (sub-band sel) and high
+  //    (sub-band sel + 2) halves, fused with 3. threshold and dual update of
+  //    those coefficients.  The item issues its global loads (old Gamma_T, or
+  //    the coarse reconstruction that replaces the low-low band below the
+  //    coarsest level) before its FMAs, so their latency overlaps the
+  //    arithmetic of the other warps.  Offsets are 32-bit within the band image.
   {
     const int Mh = M / 2;
     const int ci0 = y0 / 2 - (K - 1), cj0 = x0 / 2 - (K - 1);
-    // one coefficient: z in the cell, old Gamma_T (or coarse value) in gam
-    auto update = [&](R* cell, R gam, int gpos, bool own) {
-      if (gpos < 0) {
-        *cell = gam;
-        return;
-      }
-      const R z = *cell;
-      const R tp = soft_w<R>(z - gam * sc.inv_rho_T, sc.tau_T);
-      const R gn = gam + sc.rho_T * (tp - z);
-      *cell = gn + sc.rho_T * tp;
-      if (own) {
-        gtn[gpos] = gn;
-        if (RESID) {
-          const double dg = (double)gn - (double)gam;
-          q[Q_DGT] += (double)w * dg * dg;
-          q[Q_L1S] += (double)w * fabs((double)z);
-          if (!isfinite(gn)) q[Q_NONFIN] += 1.0;
+    for (int it = tid; it < 2 * CW * NRUN; it += WNT) {
+      const int c = it % CW, rest = it / CW;
+      const int j = rest % NRUN, sel = rest / NRUN;
+      const int gc = (cj0 + c) & (Mh - 1);
+      const bool coarse_ll = sel == 0 && rco != nullptr;  // low half replaced by R_j
+      const bool own_c = (unsigned)(c - (K - 1)) < (unsigned)(T / 2);
+      R glo[RB], ghi[RB];
+#pragma unroll
+      for (int t = 0; t < RB; t++) {
+        const int i = RB * j + t;
+        glo[t] = ghi[t] = (R)0;
+        if (i < CW) {
+          const int gi = (ci0 + i) & (Mh - 1);
+          const int plo = gi * N + gc + sel * Mh;
+          glo[t] = coarse_ll ? rco[gi * Mh + gc] : gto[plo];
+          ghi[t] = gto[plo + Mh * N];
         }
       }
-    };
-    // global offset of coefficient (row, col) of the 4 x CW x CW tile (-1: coarse band)
-    auto locate = [&](int row, int c, int& gpos, R& v) {
-      const int qd = row / CW, i = row - (row / CW) * CW;
-      const int gi = (ci0 + i) & (Mh - 1), gc = (cj0 + c) & (Mh - 1);
-      if (qd == 0 && rco != nullptr) {
-        gpos = -1;
-        v = rco[gi * Mh + gc];
-      } else {
-        gpos = (gi + (qd >> 1) * Mh) * N + gc + (qd & 1) * Mh;
-        v = gto[gpos];
-      }
-    };
-    auto owned = [&](int row, int c) {
-      const int i = row - (row / CW) * CW;
-      return (unsigned)(i - (K - 1)) < (unsigned)(T / 2) && (unsigned)(c - (K - 1)) < (unsigned)(T / 2);
-    };
-    if constexpr (CW >= 32 && CW - 32 <= 8) {
-      // groups of 4 rows per warp pass: the 32-wide heads of the 4 rows, then
-      // their tails (columns 32..CW-1) packed 8 lanes per row into one slot
-      const int lane = tid & 31, warp = tid >> 5;
-      constexpr int NG = CW;  // 4 CW rows / 4
-      for (int gidx = warp; gidx < NG; gidx += WNT / 32) {
-        const int r0 = 4 * gidx;
-        R v[5];
-        int gp[5];
+      const R* col = (sel ? rd : ra) + 2 * RB * j * B_CP + c;
+      R v[NV];
 #pragma unroll
-        for (int u = 0; u < 4; u++) locate(r0 + u, lane, gp[u], v[u]);
-        const int trow = r0 + (lane >> 3), tcol = 32 + (lane & 7);
-        const bool tail = tcol < CW;
-        if (tail) locate(trow, tcol, gp[4], v[4]);
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-          const int row = r0 + u;
-          update(sb + (row / CW) * SBQ + (row - (row / CW) * CW) * B_CP + lane, v[u], gp[u], owned(row, lane));
-        }
-        if (tail)
-          update(sb + (trow / CW) * SBQ + (trow - (trow / CW) * CW) * B_CP + tcol, v[4], gp[4], owned(trow, tcol));
-      }
-    } else {
-      // flattened over the tile, TB loads in flight per thread
-      constexpr int NQ = 4 * CW * CW;
-      constexpr int TB = 6;
-      for (int base = 0; base < NQ; base += TB * WNT) {
-        R gv[TB];
-        int gpos[TB];
-#pragma unroll
-        for (int u = 0; u < TB; u++) {
-          const int it = base + tid + u * WNT;
-          if (it < NQ) locate(it / CW, it % CW, gpos[u], gv[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < TB; u++) {
-          const int it = base + tid + u * WNT;
-          if (it < NQ) {
-            const int row = it / CW, c = it % CW;
-            update(sb + (row / CW) * SBQ + (row - (row / CW) * CW) * B_CP + c, gv[u], gpos[u], owned(row, c));
+      for (int t = 0; t < NV; t++) v[t] = col[t * B_CP];
+      R* dlo = sb + (sel ? 1 : 0) * SBQ + RB * j * B_CP + c;  // top-left / top-right
+      R* dhi = sb + (sel ? 3 : 2) * SBQ + RB * j * B_CP + c;  // bottom-left / bottom-right
+      auto update = [&](R z, R gam, int i, int dsub) -> R {
+        const R tp = soft_w<R>(z - gam * sc.inv_rho_T, sc.tau_T);
+        const R gn = gam + sc.rho_T * (tp - z);
+        if (own_c && (unsigned)(i - (K - 1)) < (unsigned)(T / 2)) {
+          const int gi = (ci0 + i) & (Mh - 1);
+          gtn[gi * N + gc + sel * Mh + dsub] = gn;
+          if (RESID) {
+            const double dg = (double)gn - (double)gam;
+            q[Q_DGT] += (double)w * dg * dg;
+            q[Q_L1S] += (double)w * fabs((double)z);
+            if (!isfinite(gn)) q[Q_NONFIN] += 1.0;
           }
         }
-      }
+        return gn + sc.rho_T * tp;
+      };
+      auto run = [&](auto with_low) {
+#pragma unroll
+        for (int i = 0; i < RB; i++) {
+          R lo = 0, hi = 0;
+#pragma unroll
+          for (int n = 0; n < F; n++) {
+            if (with_low) lo = fma(hr(n), v[2 * i + n], lo);
+            hi = fma(gr(n), v[2 * i + n], hi);
+          }
+          const int row = RB * j + i;
+          dlo[i * B_CP] = with_low ? update(lo, glo[i], row, 0) : glo[i];
+          dhi[i * B_CP] = update(hi, ghi[i], row, Mh * N);
+        }
+      };
+      if (coarse_ll) run(std::false_type());
+      else run(std::true_type());
     }
   }
   __syncthreads();
