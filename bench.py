@@ -166,6 +166,22 @@ def cpu_baseline(seconds=15.0):
             "sample": f"{n} FP64 Algorithm-1 iterations of the {SAMPLE_NAME} ({el:.1f} s)"}
 
 
+def max_over_ranks(seconds, dist=None, device="cpu"):
+    """The slowest rank's time (every rank gets it); the rank's own time without a group."""
+    if dist is None:
+        return float(seconds)
+    import torch
+
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, seconds, world):
+    """Units all ranks processed (each rank solves its own replica) per second of the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 def run_reference(args):
     rank = _env_int("RANK", 0)
     if rank != 0:
@@ -258,14 +274,10 @@ def main():
         ev1.record(stream)
         stream.synchronize()
     barrier()
-    ms = ev0.elapsed_time(ev1)
     timing = plan.timing()
     plan.set_timing(False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * V * args.steps / (ms * 1e-3)
+    ms = 1e3 * max_over_ranks(ev0.elapsed_time(ev1) * 1e-3, dist, "cuda")
+    value = whole_job_rate(V * args.steps, ms * 1e-3, world)
     launches = sum(n for _, n in timing.values())
 
     # --- end to end through the C ABI with host buffers: each step copies y from
@@ -282,12 +294,8 @@ def main():
         plan.iterate(y_dev, 1, params_e2e)
         rep = plan.report()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * V * e2e_steps / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_value = whole_job_rate(V * e2e_steps, e2e_s, world)
 
     if rank != 0:
         if dist is not None:
