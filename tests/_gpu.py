@@ -2,6 +2,9 @@
 and map its state onto the oracle's (the CUDA path keeps S and Gamma_S in the
 DCT domain and stores one Gamma_T for Db1 and Haar)."""
 
+import json
+import os
+
 import numpy as np
 import torch
 
@@ -62,9 +65,19 @@ def scales(pb, st):
 
 
 def compare(gs, os_, sc=None, keys=("X", "GP", "Sd", "GV", "GSd", "b", "GT")):
-    """max |gpu - oracle| over each array, divided by its scale (default: max |oracle|)."""
+    """max |gpu - oracle| over each array, divided by its scale (default: max |oracle|).
+    With MF_PARITY_LOG set, each comparison is appended to that file as one JSON line."""
     out = {}
     for k in keys:
         den = sc[k] if sc is not None else np.abs(os_[k]).max()
         out[k] = float(np.abs(np.asarray(gs[k]) - np.asarray(os_[k])).max() / (den if den > 0 else 1.0))
+    log_errors(out)
     return out
+
+
+def log_errors(errs):
+    """Appends errs to the file named by MF_PARITY_LOG (if set), one JSON line per call."""
+    log = os.environ.get("MF_PARITY_LOG")
+    if log:
+        with open(log, "a") as f:
+            f.write(json.dumps({"test": os.environ.get("PYTEST_CURRENT_TEST", ""), "errors": errs}) + "\n")
