@@ -86,7 +86,11 @@ __host__ __device__ constexpr int first_radix(int n) {
 // element e of transform f lives at buf[f * FS + e * ES].  Butterfly j reads
 // e = j + t n/RAD, multiplies by w^{(j mod NS) t n/(NS RAD)} (w = e^{-2 pi i/n})
 // and writes e = (j / NS) NS RAD + (j mod NS) + t NS.  tw[k] = e^{-2 pi i k/(n TWS)}.
-template <class R, int n, int RAD, int NS, int NFFT, int NT, int FS, int ES, bool FFAST, int TWS>
+// With PAD > 0 logical slot i is stored at i + (i >> PAD) (one gap every 2^PAD
+// elements), which spreads the strided writes of the first passes over the banks.
+template <int PAD> __device__ __forceinline__ int padded(int i) { return PAD ? i + (i >> PAD) : i; }
+
+template <class R, int n, int RAD, int NS, int NFFT, int NT, int FS, int ES, bool FFAST, int TWS, int PAD>
 __device__ __forceinline__ void fft_pass(cx<R>* buf, const cx<R>* __restrict__ tw) {
   constexpr int NBF = n / RAD;
   constexpr int NB = NFFT * NBF;
@@ -101,7 +105,7 @@ __device__ __forceinline__ void fft_pass(cx<R>* buf, const cx<R>* __restrict__ t
       const int jm = j & (NS - 1);
 #pragma unroll
       for (int t = 0; t < RAD; t++) {
-        cx<R> a = buf[f * FS + (j + t * NBF) * ES];
+        cx<R> a = buf[padded<PAD>(f * FS + (j + t * NBF) * ES)];
         if (NS > 1 && t > 0) a = cmul<R>(a, tw[jm * t * (n / (NS * RAD)) * TWS]);
         v[i][t] = a;
       }
@@ -118,18 +122,18 @@ __device__ __forceinline__ void fft_pass(cx<R>* buf, const cx<R>* __restrict__ t
       const int jm = j & (NS - 1);
       const int base = (j / NS) * NS * RAD + jm;
 #pragma unroll
-      for (int t = 0; t < RAD; t++) buf[f * FS + (base + t * NS) * ES] = v[i][t];
+      for (int t = 0; t < RAD; t++) buf[padded<PAD>(f * FS + (base + t * NS) * ES)] = v[i][t];
     }
   }
   __syncthreads();
 }
 
-template <class R, int n, int NS, int NFFT, int NT, int FS, int ES, bool FFAST, int TWS>
+template <class R, int n, int NS, int NFFT, int NT, int FS, int ES, bool FFAST, int TWS, int PAD = 0>
 __device__ __forceinline__ void fft_all(cx<R>* buf, const cx<R>* __restrict__ tw) {
   if constexpr (NS < n) {
     constexpr int RAD = (NS == 1) ? first_radix(n) : 8;
-    fft_pass<R, n, RAD, NS, NFFT, NT, FS, ES, FFAST, TWS>(buf, tw);
-    fft_all<R, n, NS * RAD, NFFT, NT, FS, ES, FFAST, TWS>(buf, tw);
+    fft_pass<R, n, RAD, NS, NFFT, NT, FS, ES, FFAST, TWS, PAD>(buf, tw);
+    fft_all<R, n, NS * RAD, NFFT, NT, FS, ES, FFAST, TWS, PAD>(buf, tw);
   }
 }
 
@@ -137,7 +141,11 @@ constexpr int FFT_NT = 256;
 
 // Rows per CTA of the row kernels, and columns per CTA strip of the column kernel,
 // chosen so that one CTA holds 2048 (rows) or 8192 / 4096 (columns) complex values.
-template <class R, int N> struct RowCfg { static constexpr int ROWS = (2048 / (N / 2)) > 0 ? 2048 / (N / 2) : 1; };
+template <class R, int N> struct RowCfg {
+  static constexpr int ROWS = (2048 / (N / 2)) > 0 ? 2048 / (N / 2) : 1;
+  static constexpr int PAD = 4;                                   // see padded()
+  static constexpr int SLOTS = ROWS * (N / 2) + ((ROWS * (N / 2)) >> PAD);
+};
 template <class R, int N> struct ColCfg {
   static constexpr int ELEMS = sizeof(R) == 4 ? 8192 : 4096;
   static constexpr int SW0 = ELEMS / N;
@@ -152,25 +160,26 @@ __global__ void __launch_bounds__(FFT_NT) k_rows_fwd(const R* __restrict__ in, c
                                                      int rows, const cx<R>* __restrict__ tw) {
   constexpr int n = N / 2;
   constexpr int ROWS = RowCfg<R, N>::ROWS;
+  constexpr int PAD = RowCfg<R, N>::PAD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw);
   const int row0 = blockIdx.x * ROWS;
   const cx<R>* src = reinterpret_cast<const cx<R>*>(in);
   for (int e = threadIdx.x; e < ROWS * n; e += FFT_NT) {
     const int r = e / n, m = e % n;
-    buf[e] = (row0 + r < rows) ? src[(size_t)(row0 + r) * n + m] : mk<R>(0, 0);
+    buf[padded<PAD>(e)] = (row0 + r < rows) ? src[(size_t)(row0 + r) * n + m] : mk<R>(0, 0);
   }
   __syncthreads();
-  fft_all<R, n, 1, ROWS, FFT_NT, n, 1, false, 2>(buf, tw);
+  fft_all<R, n, 1, ROWS, FFT_NT, n, 1, false, 2, PAD>(buf, tw);
   for (int e = threadIdx.x; e < ROWS * n; e += FFT_NT) {
     const int r = e / n, k = e % n;
     if (row0 + r >= rows) continue;
-    const cx<R> Zk = buf[r * n + k];
+    const cx<R> Zk = buf[padded<PAD>(r * n + k)];
     cx<R> P;
     if (k == 0) {
       P = mk<R>(Zk.x + Zk.y, Zk.x - Zk.y);  // (X[0], X[N/2]), both real
     } else {
-      const cx<R> Zm = cconj<R>(buf[r * n + (n - k)]);
+      const cx<R> Zm = cconj<R>(buf[padded<PAD>(r * n + (n - k))]);
       const cx<R> E = cscale<R>(cadd<R>(Zk, Zm), (R)0.5);
       const cx<R> D = csub<R>(Zk, Zm);
       const cx<R> O = mk<R>((R)0.5 * D.y, (R)-0.5 * D.x);  // D / (2i)
@@ -188,13 +197,14 @@ __global__ void __launch_bounds__(FFT_NT) k_rows_inv(const cx<R>* __restrict__ i
                                                      int rows, const cx<R>* __restrict__ tw) {
   constexpr int n = N / 2;
   constexpr int ROWS = RowCfg<R, N>::ROWS;
+  constexpr int PAD = RowCfg<R, N>::PAD;
   constexpr int EPT = (ROWS * n + FFT_NT - 1) / FFT_NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw);
   const int row0 = blockIdx.x * ROWS;
   for (int e = threadIdx.x; e < ROWS * n; e += FFT_NT) {
     const int r = e / n, m = e % n;
-    buf[e] = (row0 + r < rows) ? in[(size_t)(row0 + r) * n + m] : mk<R>(0, 0);
+    buf[padded<PAD>(e)] = (row0 + r < rows) ? in[(size_t)(row0 + r) * n + m] : mk<R>(0, 0);
   }
   __syncthreads();
   cx<R> z[EPT];
@@ -205,11 +215,11 @@ __global__ void __launch_bounds__(FFT_NT) k_rows_inv(const cx<R>* __restrict__ i
       const int r = e / n, k = e % n;
       cx<R> Z;
       if (k == 0) {
-        const cx<R> P = buf[r * n];
+        const cx<R> P = buf[padded<PAD>(r * n)];
         Z = mk<R>(P.x + P.y, P.x - P.y);  // E' + i O' with E' = X0 + Xn, O' = X0 - Xn
       } else {
-        const cx<R> Xk = buf[r * n + k];
-        const cx<R> Xm = cconj<R>(buf[r * n + (n - k)]);
+        const cx<R> Xk = buf[padded<PAD>(r * n + k)];
+        const cx<R> Xm = cconj<R>(buf[padded<PAD>(r * n + (n - k))]);
         const cx<R> E = cadd<R>(Xk, Xm);
         const cx<R> O = cmul<R>(csub<R>(Xk, Xm), cconj<R>(tw[k]));
         Z = mk<R>(E.x - O.y, E.y + O.x);  // E + i O
@@ -221,54 +231,81 @@ __global__ void __launch_bounds__(FFT_NT) k_rows_inv(const cx<R>* __restrict__ i
 #pragma unroll
   for (int i = 0; i < EPT; i++) {
     const int e = threadIdx.x + i * FFT_NT;
-    if (e < ROWS * n) buf[e] = z[i];
+    if (e < ROWS * n) buf[padded<PAD>(e)] = z[i];
   }
   __syncthreads();
-  fft_all<R, n, 1, ROWS, FFT_NT, n, 1, false, 2>(buf, tw);
+  fft_all<R, n, 1, ROWS, FFT_NT, n, 1, false, 2, PAD>(buf, tw);
   cx<R>* dst = reinterpret_cast<cx<R>*>(out);
   for (int e = threadIdx.x; e < ROWS * n; e += FFT_NT) {
     const int r = e / n, m = e % n;
     if (row0 + r >= rows) continue;
-    const cx<R> y = buf[e];
+    const cx<R> y = buf[padded<PAD>(e)];
     dst[(size_t)(row0 + r) * n + m] = mk<R>(y.x, -y.y);  // x[2m] = Re conj(y), x[2m+1] = Im conj(y)
   }
 }
 
 // ---------------------------------------------------------------------------
-// cols: strip of SW packed columns of one band.
+// cols: strip of SW packed columns of one band, COLS_NT threads (two
+// butterflies per thread and pass at N = 1024, so the operands of a pass stay
+// in few registers).
 // ---------------------------------------------------------------------------
-// MODE 3 applies H (X = h B) and MODE 4 applies Q^-1 alone (X = g B): both serve
-// the backward pass.
+// MODE 1: X = c + g B, then the inverse column transform (conjugate trick).
 // MODE 2 is MODE 1 plus the data-fit partials 1/2 ||y - H x||^2 (Parseval over the
 // half spectrum: interior columns count twice) read from hh/yh.
+// MODE 3 applies H (X = h B) and MODE 4 applies Q^-1 alone (X = g B): both serve
+// the backward pass.
+// The filter is applied in place in shared memory.  Packed column 0 holds the
+// DC column (A) and the Nyquist column (B) as A + iB; unpacking row ky needs
+// row (N - ky) mod N, so one thread takes both rows of a mirror pair.
+constexpr int COLS_NT = 512;
+
+template <class R, int MODE>
+struct ColFilter {
+  const cx<R>* cc;
+  const R* gg;
+  const cx<R>* hh;
+  const cx<R>* yh;
+  // X^ of one bin from B^ = Z; MODE 2 adds wfit |F(y) - N^2 h X^|^2 to fit
+  __device__ __forceinline__ cx<R> apply(cx<R> Z, size_t o, R N2, double& fit, double wfit) const {
+    cx<R> Xh;
+    if (MODE == 3) Xh = cscale<R>(cmul<R>(hh[o], Z), (R)1 / N2);
+    else if (MODE == 4) Xh = cscale<R>(Z, gg[o]);
+    else Xh = cadd<R>(cc[o], cscale<R>(Z, gg[o]));
+    if (MODE == 2) {
+      const cx<R> r = csub<R>(yh[o], cscale<R>(cmul<R>(hh[o], Xh), N2));
+      fit += wfit * ((double)r.x * r.x + (double)r.y * r.y);
+    }
+    return Xh;
+  }
+};
+
 template <class R, int N, int MODE>
-__global__ void __launch_bounds__(FFT_NT) k_cols(cx<R>* __restrict__ work, const cx<R>* __restrict__ tw,
-                                                 cx<R>* __restrict__ out_main, cx<R>* __restrict__ out_nyq,
-                                                 const cx<R>* __restrict__ cc, const cx<R>* __restrict__ cc_nyq,
-                                                 const R* __restrict__ gg, const R* __restrict__ gg_nyq,
-                                                 const cx<R>* __restrict__ hh, const cx<R>* __restrict__ hh_nyq,
-                                                 const cx<R>* __restrict__ yh, const cx<R>* __restrict__ yh_nyq,
-                                                 double* __restrict__ partials) {
+__global__ void __launch_bounds__(COLS_NT, 2) k_cols(cx<R>* __restrict__ work, const cx<R>* __restrict__ tw,
+                                                  cx<R>* __restrict__ out_main, cx<R>* __restrict__ out_nyq,
+                                                  const cx<R>* __restrict__ cc, const cx<R>* __restrict__ cc_nyq,
+                                                  const R* __restrict__ gg, const R* __restrict__ gg_nyq,
+                                                  const cx<R>* __restrict__ hh, const cx<R>* __restrict__ hh_nyq,
+                                                  const cx<R>* __restrict__ yh, const cx<R>* __restrict__ yh_nyq,
+                                                  double* __restrict__ partials) {
   constexpr int n = N / 2;          // packed columns per band
   constexpr int SW = ColCfg<R, N>::SW;
   constexpr int EL = N * SW;
-  constexpr int EPT = (EL + FFT_NT - 1) / FFT_NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw);
   const int strips = n / SW;
   const int band = blockIdx.x / strips;
   const int kx0 = (blockIdx.x % strips) * SW;
   cx<R>* base = work + (size_t)band * N * n + kx0;
-  for (int e = threadIdx.x; e < EL; e += FFT_NT) {
+  for (int e = threadIdx.x; e < EL; e += COLS_NT) {
     const int ky = e / SW, c = e % SW;
     buf[e] = base[(size_t)ky * n + c];
   }
   __syncthreads();
-  fft_all<R, N, 1, SW, FFT_NT, 1, SW, true, 1>(buf, tw);
+  fft_all<R, N, 1, SW, COLS_NT, 1, SW, true, 1>(buf, tw);
 
   if constexpr (MODE == 0) {
     // forward transform only: unpacked spectrum out
-    for (int e = threadIdx.x; e < EL; e += FFT_NT) {
+    for (int e = threadIdx.x; e < EL; e += COLS_NT) {
       const int ky = e / SW, c = e % SW, kx = kx0 + c;
       const cx<R> Z = buf[e];
       const size_t o = ((size_t)band * N + ky) * n + kx;
@@ -284,73 +321,48 @@ __global__ void __launch_bounds__(FFT_NT) k_cols(cx<R>* __restrict__ work, const
       }
     }
   } else {
-  // MODE 1: X = c + g B, then the inverse column transform (conjugate trick)
-  cx<R> z[EPT];
-  double fit = 0.0;
-  const R N2 = (R)N * (R)N;
-#pragma unroll
-  for (int i = 0; i < EPT; i++) {
-    const int e = threadIdx.x + i * FFT_NT;
-    if (e < EL) {
+    const R N2 = (R)N * (R)N;
+    const ColFilter<R, MODE> fm{cc, gg, hh, yh};
+    const ColFilter<R, MODE> fn{cc_nyq, gg_nyq, hh_nyq, yh_nyq};
+    double fit = 0.0;
+    auto unpack_row = [&](int ky, cx<R> Z, cx<R> Zmir) {
+      // row ky of column 0 from Z = buf[ky] and Zmir = buf[(N - ky) mod N]
+      const cx<R> Zm = cconj<R>(Zmir);
+      const cx<R> A = cscale<R>(cadd<R>(Z, Zm), (R)0.5);
+      const cx<R> D = csub<R>(Z, Zm);
+      const cx<R> B = mk<R>((R)0.5 * D.y, (R)-0.5 * D.x);
+      const size_t o = ((size_t)band * N + ky) * n, on = (size_t)band * N + ky;
+      const cx<R> Ax = fm.apply(A, o, N2, fit, 1.0), Bx = fn.apply(B, on, N2, fit, 1.0);
+      return cconj<R>(mk<R>(Ax.x - Bx.y, Ax.y + Bx.x));  // conj(A' + i B')
+    };
+    for (int e = threadIdx.x; e < EL; e += COLS_NT) {
       const int ky = e / SW, c = e % SW, kx = kx0 + c;
-      const cx<R> Z = buf[e];
-      const size_t o = ((size_t)band * N + ky) * n + kx;
-      cx<R> Xh;
       if (kx == 0) {
-        const cx<R> Zm = cconj<R>(buf[((N - ky) % N) * SW]);
-        const cx<R> A = cscale<R>(cadd<R>(Z, Zm), (R)0.5);
-        const cx<R> D = csub<R>(Z, Zm);
-        const cx<R> B = mk<R>((R)0.5 * D.y, (R)-0.5 * D.x);
-        const size_t on = (size_t)band * N + ky;
-        cx<R> Ax, Bx;
-        if (MODE == 3) {  // H: multiply by the transfer function (1/N^2 of the inverse folded in)
-          Ax = cscale<R>(cmul<R>(hh[o], A), (R)1 / N2);
-          Bx = cscale<R>(cmul<R>(hh_nyq[on], B), (R)1 / N2);
-        } else if (MODE == 4) {  // Q^-1 without the H^T y term
-          Ax = cscale<R>(A, gg[o]);
-          Bx = cscale<R>(B, gg_nyq[on]);
-        } else {
-          Ax = cadd<R>(cc[o], cscale<R>(A, gg[o]));
-          Bx = cadd<R>(cc_nyq[on], cscale<R>(B, gg_nyq[on]));
-        }
-        Xh = mk<R>(Ax.x - Bx.y, Ax.y + Bx.x);  // A' + i B'
-        if (MODE == 2) {
-          const cx<R> ra = csub<R>(yh[o], cscale<R>(cmul<R>(hh[o], Ax), N2));
-          const cx<R> rb = csub<R>(yh_nyq[on], cscale<R>(cmul<R>(hh_nyq[on], Bx), N2));
-          fit += (double)ra.x * ra.x + (double)ra.y * ra.y + (double)rb.x * rb.x + (double)rb.y * rb.y;
-        }
+        if (ky > N / 2) continue;  // the partner of a pair with ky < N/2
+        const int km = (N - ky) & (N - 1);
+        const cx<R> Z = buf[ky * SW], Zp = buf[km * SW];
+        const cx<R> v = unpack_row(ky, Z, Zp);
+        if (km != ky) buf[km * SW] = unpack_row(km, Zp, Z);
+        buf[ky * SW] = v;
       } else {
-        if (MODE == 3) Xh = cscale<R>(cmul<R>(hh[o], Z), (R)1 / N2);
-        else if (MODE == 4) Xh = cscale<R>(Z, gg[o]);
-        else Xh = cadd<R>(cc[o], cscale<R>(Z, gg[o]));
-        if (MODE == 2) {
-          const cx<R> r = csub<R>(yh[o], cscale<R>(cmul<R>(hh[o], Xh), N2));
-          fit += 2.0 * ((double)r.x * r.x + (double)r.y * r.y);
-        }
+        const size_t o = ((size_t)band * N + ky) * n + kx;
+        buf[e] = cconj<R>(fm.apply(buf[e], o, N2, fit, 2.0));
       }
-      z[i] = cconj<R>(Xh);
     }
-  }
-  __syncthreads();
+    __syncthreads();
+    fft_all<R, N, 1, SW, COLS_NT, 1, SW, true, 1>(buf, tw);
+    for (int e = threadIdx.x; e < EL; e += COLS_NT) {
+      const int ky = e / SW, c = e % SW;
+      base[(size_t)ky * n + c] = cconj<R>(buf[e]);
+    }
+    if (MODE == 2) {
+      double q[Q_COUNT];
 #pragma unroll
-  for (int i = 0; i < EPT; i++) {
-    const int e = threadIdx.x + i * FFT_NT;
-    if (e < EL) buf[e] = z[i];
-  }
-  __syncthreads();
-  fft_all<R, N, 1, SW, FFT_NT, 1, SW, true, 1>(buf, tw);
-  for (int e = threadIdx.x; e < EL; e += FFT_NT) {
-    const int ky = e / SW, c = e % SW;
-    base[(size_t)ky * n + c] = cconj<R>(buf[e]);
-  }
-  if (MODE == 2) {
-    double q[Q_COUNT];
-#pragma unroll
-    for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
-    q[Q_XMIN] = 1e300;
-    q[Q_FIT] = 0.5 * fit / ((double)N * (double)N);
-    block_reduce_write<FFT_NT>(q, partials + (size_t)blockIdx.x * MF_NQ);
-  }
+      for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
+      q[Q_XMIN] = 1e300;
+      q[Q_FIT] = 0.5 * fit / ((double)N * (double)N);
+      block_reduce_write<COLS_NT>(q, partials + (size_t)blockIdx.x * MF_NQ);
+    }
   }
 }
 
@@ -374,7 +386,7 @@ __global__ void k_constants(const cx<R>* __restrict__ hh, const cx<R>* __restric
 template <class R, int N>
 static cudaError_t rows_fwd_n(const R* in, cx<R>* out, int rows, const cx<R>* tw, cudaStream_t s) {
   constexpr int ROWS = RowCfg<R, N>::ROWS;
-  const size_t sm = sizeof(cx<R>) * ROWS * (N / 2);
+  const size_t sm = sizeof(cx<R>) * RowCfg<R, N>::SLOTS;
   cudaError_t e = cudaFuncSetAttribute(k_rows_fwd<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k_rows_fwd<R, N><<<(rows + ROWS - 1) / ROWS, FFT_NT, sm, s>>>(in, out, rows, tw);
@@ -383,7 +395,7 @@ static cudaError_t rows_fwd_n(const R* in, cx<R>* out, int rows, const cx<R>* tw
 template <class R, int N>
 static cudaError_t rows_inv_n(const cx<R>* in, R* out, int rows, const cx<R>* tw, cudaStream_t s) {
   constexpr int ROWS = RowCfg<R, N>::ROWS;
-  const size_t sm = sizeof(cx<R>) * ROWS * (N / 2);
+  const size_t sm = sizeof(cx<R>) * RowCfg<R, N>::SLOTS;
   cudaError_t e = cudaFuncSetAttribute(k_rows_inv<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k_rows_inv<R, N><<<(rows + ROWS - 1) / ROWS, FFT_NT, sm, s>>>(in, out, rows, tw);
@@ -398,7 +410,7 @@ static cudaError_t cols_mode(cx<R>* work, int L, const cx<R>* tw, cx<R>* om, cx<
   const int blocks = L * ((N / 2) / SW);
   cudaError_t e = cudaFuncSetAttribute(k_cols<R, N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_cols<R, N, MODE><<<blocks, FFT_NT, sm, s>>>(work, tw, om, on, cc, ccn, gg, ggn, hh, hhn, yh, yhn, partials);
+  k_cols<R, N, MODE><<<blocks, COLS_NT, sm, s>>>(work, tw, om, on, cc, ccn, gg, ggn, hh, hhn, yh, yhn, partials);
   return cudaGetLastError();
 }
 template <class R, int N>

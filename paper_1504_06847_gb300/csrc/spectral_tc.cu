@@ -182,11 +182,6 @@ __global__ void __launch_bounds__(TC_NT, 2) k_spectral_tc(const float* __restric
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(bmats);
-    uint4* dst = reinterpret_cast<uint4*>(B1hi);
-    for (int e = tid; e < 4 * LP * LP / 8; e += TC_NT) dst[e] = src[e];
-  }
   // this pixel's half spectrum: FP32 copy and the split A operand
   {
     float v[HL];
@@ -194,6 +189,24 @@ __global__ void __launch_bounds__(TC_NT, 2) k_spectral_tc(const float* __restric
     for (int t = 0; t < HL; t++) {
       const int l = half * HL + t;
       v[t] = l < L ? X[(size_t)l * NN + p] : 0.f;
+    }
+    // L2 prefetch of the tile's rows of S, Gamma_V, Gamma_S (read after the first
+    // product) and Gamma_P (after the second): one 128-byte line per warp-row
+    // segment, so the later phases find them in L2 instead of waiting on HBM.
+    {
+      const size_t p0 = (size_t)blockIdx.x * TC_M;
+      for (int e = tid; e < 4 * L * (TC_M / 32); e += TC_NT) {
+        const int seg = e % (TC_M / 32), rest = e / (TC_M / 32);
+        const int l = rest % L, a = rest / L;
+        const float* base = a == 0 ? Sd : a == 1 ? GV : a == 2 ? GSd : GP;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (size_t)l * NN + p0 + 32 * seg));
+      }
+    }
+    {
+      // the DCT operands (L2-resident, shared by every CTA)
+      const uint4* src = reinterpret_cast<const uint4*>(bmats);
+      uint4* dst = reinterpret_cast<uint4*>(B1hi);
+      for (int e = tid; e < 4 * LP * LP / 8; e += TC_NT) dst[e] = src[e];
     }
 #pragma unroll
     for (int c0 = 0; c0 < HL; c0 += 8) {

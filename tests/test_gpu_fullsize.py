@@ -53,6 +53,5 @@ def test_splitbf16_1024x1024x64_full_state():
         "x_norm2": abs(rep["x_norm2"] - H[-1, 5]) / H[-1, 5],
     }
     _gpu.log_errors(red)
-    assert red["objective"] < 1e-4 and red["x_norm2"] < 1e-4, red
-    assert red["primal_res"] < 1e-2 and red["dual_gamma"] < 1e-2, red
+    assert max(red.values()) < 1e-4, red
     assert abs(rep["x_min"] - H[-1, 4]) <= 1e-4 * np.abs(st["X"]).max()
