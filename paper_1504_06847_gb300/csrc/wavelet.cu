@@ -54,6 +54,8 @@ template <> struct Taps<double> {
   static __device__ __forceinline__ double g(int K, int n) { return c_gd[K][n]; }
 };
 
+cudaError_t upload_tap_pairs();
+
 cudaError_t upload_taps() {
   float hf[MF_MAX_K + 1][MF_MAX_F] = {}, gf[MF_MAX_K + 1][MF_MAX_F] = {};
   double hd[MF_MAX_K + 1][MF_MAX_F] = {}, gd[MF_MAX_K + 1][MF_MAX_F] = {};
@@ -71,6 +73,7 @@ cudaError_t upload_taps() {
   if (!e) e = cudaMemcpyToSymbol(c_gf, gf, sizeof(gf));
   if (!e) e = cudaMemcpyToSymbol(c_hd, hd, sizeof(hd));
   if (!e) e = cudaMemcpyToSymbol(c_gd, gd, sizeof(gd));
+  if (!e) e = upload_tap_pairs();
   return e;
 }
 
@@ -344,6 +347,8 @@ struct TC {
   static constexpr int OPI = (T * T / WNT) < 8 ? (T * T / WNT) : 8;  // outputs of one synthesis item
   static constexpr int IPT = T * T / (WNT * OPI);                    // synthesis items per thread
   static constexpr int MINB = T == 64 ? 2 : 4;                       // CTAs per SM
+  // the pair planes that follow the input tile start on a 16-byte boundary
+  static_assert((IR * IP) % 2 == 0, "input tile size must keep the pair planes aligned");
 };
 
 template <class R, int T>
@@ -356,29 +361,102 @@ __device__ __forceinline__ R* tile_smem(R*& ra, R*& rd, R*& sb) {
   return in;
 }
 
+// Pairs of values that travel together through one level: the {low, high}
+// outputs of the row analysis, the {top-left, top-right} and {bottom-left,
+// bottom-right} sub-bands of the column analysis, and the {low, high} parts of
+// the column synthesis.  For FP32 a pair is one 64-bit register and shared
+// memory word, and each filter tap is one packed FMA (fma.rn.f32x2, two IEEE
+// FMAs with round-to-nearest) on both members.
+template <class R> struct V2;
+template <> struct V2<float> { typedef float2 T; };
+template <> struct V2<double> { typedef double2 T; };
+
+__device__ __forceinline__ float2 mk2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk2(double a, double b) { return make_double2(a, b); }
+
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 pa, pb, pc, pd;\n\t"
+      "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\tmov.b64 pc, {%6, %7};\n\t"
+      "fma.rn.f32x2 pd, pa, pb, pc;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+
+// Tap pairs by half-length K: {h_n, h_n}, {g_n, g_n} and {h_n, g_n}.
+__constant__ float2 c_hh2f[MF_MAX_K + 1][MF_MAX_F];
+__constant__ float2 c_gg2f[MF_MAX_K + 1][MF_MAX_F];
+__constant__ float2 c_hg2f[MF_MAX_K + 1][MF_MAX_F];
+__constant__ double2 c_hh2d[MF_MAX_K + 1][MF_MAX_F];
+__constant__ double2 c_gg2d[MF_MAX_K + 1][MF_MAX_F];
+__constant__ double2 c_hg2d[MF_MAX_K + 1][MF_MAX_F];
+
+template <class R> struct Taps2;
+template <> struct Taps2<float> {
+  static __device__ __forceinline__ float2 hh(int K, int n) { return c_hh2f[K][n]; }
+  static __device__ __forceinline__ float2 gg(int K, int n) { return c_gg2f[K][n]; }
+  static __device__ __forceinline__ float2 hg(int K, int n) { return c_hg2f[K][n]; }
+};
+template <> struct Taps2<double> {
+  static __device__ __forceinline__ double2 hh(int K, int n) { return c_hh2d[K][n]; }
+  static __device__ __forceinline__ double2 gg(int K, int n) { return c_gg2d[K][n]; }
+  static __device__ __forceinline__ double2 hg(int K, int n) { return c_hg2d[K][n]; }
+};
+
+cudaError_t upload_tap_pairs() {
+  float2 hhf[MF_MAX_K + 1][MF_MAX_F] = {}, ggf[MF_MAX_K + 1][MF_MAX_F] = {}, hgf[MF_MAX_K + 1][MF_MAX_F] = {};
+  double2 hhd[MF_MAX_K + 1][MF_MAX_F] = {}, ggd[MF_MAX_K + 1][MF_MAX_F] = {}, hgd[MF_MAX_K + 1][MF_MAX_F] = {};
+  for (int K = 1; K <= MF_MAX_K; K++) {
+    const double* h = filter_taps(K);
+    for (int n = 0; n < 2 * K; n++) {
+      const double gv = (n & 1) ? -h[2 * K - 1 - n] : h[2 * K - 1 - n];
+      hhd[K][n] = make_double2(h[n], h[n]);
+      ggd[K][n] = make_double2(gv, gv);
+      hgd[K][n] = make_double2(h[n], gv);
+      hhf[K][n] = make_float2((float)h[n], (float)h[n]);
+      ggf[K][n] = make_float2((float)gv, (float)gv);
+      hgf[K][n] = make_float2((float)h[n], (float)gv);
+    }
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_hh2f, hhf, sizeof(hhf));
+  if (!e) e = cudaMemcpyToSymbol(c_gg2f, ggf, sizeof(ggf));
+  if (!e) e = cudaMemcpyToSymbol(c_hg2f, hgf, sizeof(hgf));
+  if (!e) e = cudaMemcpyToSymbol(c_hh2d, hhd, sizeof(hhd));
+  if (!e) e = cudaMemcpyToSymbol(c_gg2d, ggd, sizeof(ggd));
+  if (!e) e = cudaMemcpyToSymbol(c_hg2d, hgd, sizeof(hgd));
+  return e;
+}
+
 // One basis (half-length K) on one T x T output tile.  in: input tile with
 // pitch TC<T>::IP, loaded for half-length Kin >= K at offset off = 2 (Kin - K).
+// rpair: TC<T>::CR x TC<T>::CP pairs (row analysis, then column synthesis);
+// spair: two TC<T>::SR x TC<T>::CP planes of sub-band pairs.
 // emit(s, m, x, v[OPI]) receives output row m, columns x..x+OPI-1 for the
 // thread's item s (fixed across calls).
 template <class R, int T, int K, int RESID, class Emit>
-__device__ __forceinline__ void level_tile_t(const R* in, int off, R* ra, R* rd, R* sb, const R* __restrict__ h,
-                                             const R* __restrict__ g, int M, int y0, int x0,
+__device__ __forceinline__ void level_tile_t(const R* in, int off, R* rpair, R* spair, int M, int y0, int x0,
                                              const R* __restrict__ gto, R* __restrict__ gtn, int N,
                                              const R* __restrict__ rco, const IterScalars<R>& sc, R w, double* q,
                                              Emit emit) {
   typedef TC<T> C;
+  typedef typename V2<R>::T P;
   constexpr int F = 2 * K;
   constexpr int CW = T / 2 + K - 1;     // coefficients per tile edge (with the synthesis halo)
   constexpr int IH = T + 4 * K - 4;     // input rows used
   constexpr int RB = C::RB;             // outputs per thread run
-  constexpr int B_IP = C::IP, B_CP = C::CP, SBQ = C::SBQ, OPI = C::OPI;
+  constexpr int B_IP = C::IP, B_CP = C::CP, OPI = C::OPI;
   constexpr int NRUN = (CW + RB - 1) / RB;
   constexpr int NV = 2 * RB - 2 + F;    // inputs of a run of RB analysis outputs
   constexpr int NU = RB / 2 + K - 1;    // coefficients of a run of RB synthesis outputs
+  P* rp = reinterpret_cast<P*>(rpair);
+  P* top = reinterpret_cast<P*>(spair);  // {top-left, top-right}: low rows of the low / high columns
+  P* bot = top + C::SR * B_CP;           // {bottom-left, bottom-right}: high rows
   const int tid = threadIdx.x;
-#define hr(n) Taps<R>::h(K, n)
-#define gr(n) Taps<R>::g(K, n)
-  // 1. row analysis: row r, coefficients RB j..RB j+RB-1 (low into ra, high into rd);
+  // 1. row analysis: row r, coefficient pairs {low, high} RB j..RB j+RB-1;
   //    consecutive threads take consecutive rows
   for (int it = tid; it < IH * NRUN; it += WNT) {
     const int r = it % IH, j = it / IH;
@@ -386,61 +464,53 @@ __device__ __forceinline__ void level_tile_t(const R* in, int off, R* ra, R* rd,
     R v[NV];
 #pragma unroll
     for (int t = 0; t < NV; t++) v[t] = src[t];
-    R* da = ra + r * B_CP + RB * j;
-    R* dd = rd + r * B_CP + RB * j;
+    P* dst = rp + r * B_CP + RB * j;
 #pragma unroll
     for (int c = 0; c < RB; c++) {
-      R a = 0, d = 0;
+      P acc = mk2((R)0, (R)0);
 #pragma unroll
-      for (int n = 0; n < F; n++) {
-        a = fma(hr(n), v[2 * c + n], a);
-        d = fma(gr(n), v[2 * c + n], d);
-      }
-      da[c] = a;
-      dd[c] = d;
+      for (int n = 0; n < F; n++) acc = fma2(Taps2<R>::hg(K, n), mk2(v[2 * c + n], v[2 * c + n]), acc);
+      dst[c] = acc;
     }
   }
   __syncthreads();
-  // 2. column analysis of column c of ra (sel 0) or rd (sel 1) into
-  //    coefficient rows RB j..RB j+RB-1 of the low (sub-band sel) and high
-  //    (sub-band sel + 2) halves, fused with 3. threshold and dual update of
-  //    those coefficients.  The item issues its global loads (old Gamma_T, or
-  //    the coarse reconstruction that replaces the low-low band below the
-  //    coarsest level) before its FMAs, so their latency overlaps the
-  //    arithmetic of the other warps.  Offsets are 32-bit within the band image.
+  // 2. column analysis of column c of both row-analysis outputs into coefficient
+  //    rows RB j..RB j+RB-1 of the four sub-bands, fused with 3. threshold and
+  //    dual update of those coefficients.  The item issues its global loads (old
+  //    Gamma_T, or the coarse reconstruction that replaces the low-low band below
+  //    the coarsest level) before its FMAs.  Offsets are 32-bit within the band.
   {
     const int Mh = M / 2;
     const int ci0 = y0 / 2 - (K - 1), cj0 = x0 / 2 - (K - 1);
-    for (int it = tid; it < 2 * CW * NRUN; it += WNT) {
-      const int c = it % CW, rest = it / CW;
-      const int j = rest % NRUN, sel = rest / NRUN;
+    const int MhN = Mh * N;
+    for (int it = tid; it < CW * NRUN; it += WNT) {
+      const int c = it % CW, j = it / CW;
       const int gc = (cj0 + c) & (Mh - 1);
-      const bool coarse_ll = sel == 0 && rco != nullptr;  // low half replaced by R_j
       const bool own_c = (unsigned)(c - (K - 1)) < (unsigned)(T / 2);
-      R glo[RB], ghi[RB];
+      R gtl[RB], gtr[RB], gbl[RB], gbr[RB];
+      int go[RB];
 #pragma unroll
-      for (int t = 0; t < RB; t++) {
-        const int i = RB * j + t;
-        glo[t] = ghi[t] = (R)0;
-        if (i < CW) {
-          const int gi = (ci0 + i) & (Mh - 1);
-          const int plo = gi * N + gc + sel * Mh;
-          glo[t] = coarse_ll ? rco[gi * Mh + gc] : gto[plo];
-          ghi[t] = gto[plo + Mh * N];
+      for (int i = 0; i < RB; i++) {
+        const int row = RB * j + i;
+        const int gi = (ci0 + row) & (Mh - 1);
+        go[i] = gi * N + gc;
+        gtl[i] = gtr[i] = gbl[i] = gbr[i] = (R)0;
+        if (row < CW) {
+          gtl[i] = rco != nullptr ? rco[gi * Mh + gc] : gto[go[i]];
+          gtr[i] = gto[go[i] + Mh];
+          gbl[i] = gto[go[i] + MhN];
+          gbr[i] = gto[go[i] + MhN + Mh];
         }
       }
-      const R* col = (sel ? rd : ra) + 2 * RB * j * B_CP + c;
-      R v[NV];
+      const P* col = rp + 2 * RB * j * B_CP + c;
+      P v[NV];
 #pragma unroll
       for (int t = 0; t < NV; t++) v[t] = col[t * B_CP];
-      R* dlo = sb + (sel ? 1 : 0) * SBQ + RB * j * B_CP + c;  // top-left / top-right
-      R* dhi = sb + (sel ? 3 : 2) * SBQ + RB * j * B_CP + c;  // bottom-left / bottom-right
-      auto update = [&](R z, R gam, int i, int dsub) -> R {
+      auto update = [&](R z, R gam, bool own, int pos) -> R {
         const R tp = soft_w<R>(z - gam * sc.inv_rho_T, sc.tau_T);
         const R gn = gam + sc.rho_T * (tp - z);
-        if (own_c && (unsigned)(i - (K - 1)) < (unsigned)(T / 2)) {
-          const int gi = (ci0 + i) & (Mh - 1);
-          gtn[gi * N + gc + sel * Mh + dsub] = gn;
+        if (own) {
+          gtn[pos] = gn;
           if (RESID) {
             const double dg = (double)gn - (double)gam;
             q[Q_DGT] += (double)w * dg * dg;
@@ -450,55 +520,53 @@ __device__ __forceinline__ void level_tile_t(const R* in, int off, R* ra, R* rd,
         }
         return gn + sc.rho_T * tp;
       };
-      auto run = [&](auto with_low) {
 #pragma unroll
-        for (int i = 0; i < RB; i++) {
-          R lo = 0, hi = 0;
+      for (int i = 0; i < RB; i++) {
+        P lo = mk2((R)0, (R)0), hi = mk2((R)0, (R)0);
 #pragma unroll
-          for (int n = 0; n < F; n++) {
-            if (with_low) lo = fma(hr(n), v[2 * i + n], lo);
-            hi = fma(gr(n), v[2 * i + n], hi);
-          }
-          const int row = RB * j + i;
-          dlo[i * B_CP] = with_low ? update(lo, glo[i], row, 0) : glo[i];
-          dhi[i * B_CP] = update(hi, ghi[i], row, Mh * N);
+        for (int n = 0; n < F; n++) {
+          lo = fma2(Taps2<R>::hh(K, n), v[2 * i + n], lo);
+          hi = fma2(Taps2<R>::gg(K, n), v[2 * i + n], hi);
         }
-      };
-      if (coarse_ll) run(std::false_type());
-      else run(std::true_type());
+        const int row = RB * j + i;
+        const bool own = own_c && (unsigned)(row - (K - 1)) < (unsigned)(T / 2);
+        const R tl = rco != nullptr ? gtl[i] : update(lo.x, gtl[i], own, go[i]);
+        top[row * B_CP + c] = mk2(tl, update(lo.y, gtr[i], own, go[i] + Mh));
+        bot[row * B_CP + c] = mk2(update(hi.x, gbl[i], own, go[i] + MhN), update(hi.y, gbr[i], own, go[i] + MhN + Mh));
+      }
     }
   }
   __syncthreads();
-  // 4. column synthesis: output rows RB j.. of coefficient column c; low part
-  //    (from the two left sub-bands) into ra, high part (right sub-bands) into rd
-  for (int it = tid; it < 2 * CW * (T / RB); it += WNT) {
-    const int c = it % CW, rest = it / CW;
-    const int j = rest % (T / RB), sel = rest / (T / RB);
-    const R* Ua = sb + (sel ? 1 : 0) * SBQ + (RB / 2) * j * B_CP + c;
-    const R* Ud = sb + (sel ? 3 : 2) * SBQ + (RB / 2) * j * B_CP + c;
-    R ua[NU], ud[NU];
+  // 4. column synthesis: output rows RB j.. of coefficient column c; the pair
+  //    {low part, high part} comes from {TL, TR} and {BL, BR} with the same taps
+  for (int it = tid; it < CW * (T / RB); it += WNT) {
+    const int c = it % CW, j = it / CW;
+    const P* ut = top + (RB / 2) * j * B_CP + c;
+    const P* ub = bot + (RB / 2) * j * B_CP + c;
+    P ua[NU], ud[NU];
 #pragma unroll
     for (int ii = 0; ii < NU; ii++) {
-      ua[ii] = Ua[ii * B_CP];
-      ud[ii] = Ud[ii * B_CP];
+      ua[ii] = ut[ii * B_CP];
+      ud[ii] = ub[ii * B_CP];
     }
-    R* dst = (sel ? rd : ra) + RB * j * B_CP + c;
+    P* dst = rp + RB * j * B_CP + c;
 #pragma unroll
     for (int t = 0; t < RB; t++) {
       const int par = t & 1;
-      R acc = 0;
+      P acc = mk2((R)0, (R)0);
 #pragma unroll
       for (int n2 = 0; n2 < K; n2++) {
         const int n = 2 * n2 + par;
         const int ii = (t - par) / 2 - n2 + K - 1;
-        acc = fma(hr(n), ua[ii], fma(gr(n), ud[ii], acc));
+        acc = fma2(Taps2<R>::hh(K, n), ua[ii], fma2(Taps2<R>::gg(K, n), ud[ii], acc));
       }
       dst[t * B_CP] = acc;
     }
   }
   __syncthreads();
-  // 5. row synthesis: output row m, columns OPI j..OPI j+OPI-1 (runs of RS);
-  //    consecutive threads take consecutive rows
+  // 5. row synthesis: output row m, columns OPI j..OPI j+OPI-1 (runs of RS) from
+  //    the {low, high} pairs with the {h, g} tap pairs; consecutive threads take
+  //    consecutive rows
   {
     constexpr int RS = OPI < RB ? OPI : RB;
     constexpr int NS = RS / 2 + K - 1;
@@ -509,32 +577,26 @@ __device__ __forceinline__ void level_tile_t(const R* in, int off, R* ra, R* rd,
       R out[OPI];
 #pragma unroll
       for (int hh = 0; hh < OPI / RS; hh++) {
-        const R* cl = ra + m * B_CP + (OPI / 2) * j + (RS / 2) * hh;
-        const R* ch = rd + m * B_CP + (OPI / 2) * j + (RS / 2) * hh;
-        R ua[NS], ud[NS];
+        const P* cl = rp + m * B_CP + (OPI / 2) * j + (RS / 2) * hh;
+        P u[NS];
 #pragma unroll
-        for (int ii = 0; ii < NS; ii++) {
-          ua[ii] = cl[ii];
-          ud[ii] = ch[ii];
-        }
+        for (int ii = 0; ii < NS; ii++) u[ii] = cl[ii];
 #pragma unroll
         for (int t = 0; t < RS; t++) {
           const int par = t & 1;
-          R acc = 0;
+          P acc = mk2((R)0, (R)0);
 #pragma unroll
           for (int n2 = 0; n2 < K; n2++) {
             const int n = 2 * n2 + par;
             const int ii = (t - par) / 2 - n2 + K - 1;
-            acc = fma(hr(n), ua[ii], fma(gr(n), ud[ii], acc));
+            acc = fma2(Taps2<R>::hg(K, n), u[ii], acc);
           }
-          out[RS * hh + t] = acc;
+          out[RS * hh + t] = acc.x + acc.y;
         }
       }
       emit(s, m, OPI * j, out);
     }
   }
-#undef hr
-#undef gr
 }
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -580,8 +642,7 @@ __device__ __noinline__ void level1_basis(const R* in, R* ra, R* rd, R* sb, R* b
 #pragma unroll
     for (int t = 0; t < TC<T>::OPI; t++) a[t] = fma(w, v[t], a[t]);
   };
-  level_tile_t<R, T, K, RESID>(in, 2 * (MF_MAX_K - K), ra, rd, sb, nullptr, nullptr, N, y0, x0, gto, gtn, N, rco,
-                               sc, w, q, emit);
+  level_tile_t<R, T, K, RESID>(in, 2 * (MF_MAX_K - K), ra, sb, N, y0, x0, gto, gtn, N, rco, sc, w, q, emit);
 }
 
 template <class R, int T, int RESID>
@@ -648,7 +709,7 @@ __device__ __noinline__ void levelj_basis(const R* __restrict__ src, R* in, R* r
   };
   load_tile_t<R, T>(src, M, y0 - 2 * K + 2, x0 - 2 * K + 2, T + 4 * K - 4, in);
   __syncthreads();
-  level_tile_t<R, T, K, RESID>(in, 0, ra, rd, sb, nullptr, nullptr, M, y0, x0, gto, gtn, N, rco, sc, w, q, emit);
+  level_tile_t<R, T, K, RESID>(in, 0, ra, sb, M, y0, x0, gto, gtn, N, rco, sc, w, q, emit);
 }
 
 // L2 prefetch of a basis's input tile at a coarser level.
