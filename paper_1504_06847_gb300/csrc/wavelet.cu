@@ -82,15 +82,26 @@ template <class R> __device__ __forceinline__ R soft_w(R t, R tau) {
   return a > (R)0 ? copysign(a, t) : (R)0;
 }
 
+// Asynchronous global -> shared copy of one element (cp.async: the thread does
+// not wait for the data, so all of a tile's copies are in flight at once).
+template <class R>
+__device__ __forceinline__ void cp_async_elem(R* dst, const R* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src),
+               "n"((int)sizeof(R))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Loads rows/cols [r0, r0 + H) x [c0, c0 + W) of an M x M image (periodic) into
-// dst with pitch P.
+// dst with pitch P.  The caller synchronises the CTA before reading dst.
 template <class R>
 __device__ __forceinline__ void load_tile(const R* __restrict__ img, int M, int r0, int c0, int H, int W, R* dst,
                                           int P) {
   for (int e = threadIdx.x; e < H * W; e += WNT) {
     const int r = e / W, c = e % W;
-    dst[r * P + c] = img[(size_t)((r0 + r) & (M - 1)) * M + ((c0 + c) & (M - 1))];
+    cp_async_elem(dst + r * P + c, img + (size_t)((r0 + r) & (M - 1)) * M + ((c0 + c) & (M - 1)));
   }
+  cp_async_wait_all();
 }
 
 // Fused level on one output tile for the basis with half-length K.
@@ -625,8 +636,9 @@ template <class R, int T>
 __device__ __forceinline__ void load_tile_t(const R* __restrict__ img, int M, int r0, int c0, int H, R* dst) {
   for (int r = threadIdx.x >> 5; r < H; r += WNT / 32) {
     const R* src = img + (size_t)((r0 + r) & (M - 1)) * M;
-    for (int c = threadIdx.x & 31; c < H; c += 32) dst[r * TC<T>::IP + c] = src[(c0 + c) & (M - 1)];
+    for (int c = threadIdx.x & 31; c < H; c += 32) cp_async_elem(dst + r * TC<T>::IP + c, src + ((c0 + c) & (M - 1)));
   }
+  cp_async_wait_all();
 }
 
 // One basis of level 1 on a T x T tile, adding w W_k^T U_k into the shared
