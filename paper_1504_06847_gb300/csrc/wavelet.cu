@@ -447,12 +447,13 @@ cudaError_t upload_tap_pairs() {
 // rpair: TC<T>::CR x TC<T>::CP pairs (row analysis, then column synthesis);
 // spair: two TC<T>::SR x TC<T>::CP planes of sub-band pairs.
 // emit(s, m, x, v[OPI]) receives output row m, columns x..x+OPI-1 for the
-// thread's item s (fixed across calls).
-template <class R, int T, int K, int RESID, class Emit>
+// thread's item s (fixed across calls); after_rows() runs once the input tile
+// has been consumed (all threads past the row analysis).
+template <class R, int T, int K, int RESID, class Emit, class AfterRows>
 __device__ __forceinline__ void level_tile_t(const R* in, int off, R* rpair, R* spair, int M, int y0, int x0,
                                              const R* __restrict__ gto, R* __restrict__ gtn, int N,
                                              const R* __restrict__ rco, const IterScalars<R>& sc, R w, double* q,
-                                             Emit emit) {
+                                             Emit emit, AfterRows after_rows) {
   typedef TC<T> C;
   typedef typename V2<R>::T P;
   constexpr int F = 2 * K;
@@ -485,6 +486,7 @@ __device__ __forceinline__ void level_tile_t(const R* in, int off, R* rpair, R* 
     }
   }
   __syncthreads();
+  after_rows();  // the input tile is free from here on
   // 2. column analysis of column c of both row-analysis outputs into coefficient
   //    rows RB j..RB j+RB-1 of the four sub-bands, fused with 3. threshold and
   //    dual update of those coefficients.  The item issues its global loads (old
@@ -638,7 +640,6 @@ __device__ __forceinline__ void load_tile_t(const R* __restrict__ img, int M, in
     const R* src = img + (size_t)((r0 + r) & (M - 1)) * M;
     for (int c = threadIdx.x & 31; c < H; c += 32) cp_async_elem(dst + r * TC<T>::IP + c, src + ((c0 + c) & (M - 1)));
   }
-  cp_async_wait_all();
 }
 
 // One basis of level 1 on a T x T tile, adding w W_k^T U_k into the shared
@@ -654,7 +655,8 @@ __device__ __noinline__ void level1_basis(const R* in, R* ra, R* rd, R* sb, R* b
 #pragma unroll
     for (int t = 0; t < TC<T>::OPI; t++) a[t] = fma(w, v[t], a[t]);
   };
-  level_tile_t<R, T, K, RESID>(in, 2 * (MF_MAX_K - K), ra, sb, N, y0, x0, gto, gtn, N, rco, sc, w, q, emit);
+  level_tile_t<R, T, K, RESID>(in, 2 * (MF_MAX_K - K), ra, sb, N, y0, x0, gto, gtn, N, rco, sc, w, q, emit,
+                               [] {});
 }
 
 template <class R, int T, int RESID>
@@ -672,6 +674,7 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_level1_t(const R* __re
   const int y0 = (blockIdx.x / tpd) * T, x0 = (blockIdx.x % tpd) * T;
   const size_t NN = (size_t)N * N;
   load_tile_t<R, T>(X + band * NN, N, y0 - 2 * MF_MAX_K + 2, x0 - 2 * MF_MAX_K + 2, C::IR, in);
+  cp_async_wait_all();
   for (int r = threadIdx.x; r < T * (T / 32); r += WNT)  // the b tile read at the end
     prefetch_l2(b + band * NN + (size_t)(y0 + r / (T / 32)) * N + x0 + 32 * (r % (T / 32)));
   if (ws->nd > 0)
@@ -708,20 +711,26 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_level1_t(const R* __re
   if (RESID) block_reduce_write<WNT>(q, partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * MF_NQ);
 }
 
-// One basis of a coarser level on a T x T tile: loads its input tile and writes
-// the level's synthesis into R_{j-1}.  Not inlined (see level1_basis).
+// One basis of a coarser level on a T x T tile (its input tile already in
+// shared memory); writes the level's synthesis into R_{j-1} and, once the tile
+// is consumed, starts the asynchronous copy of the next basis's tile (next_src,
+// half-length next_K; none when next_src is null).  Not inlined (see
+// level1_basis).
 template <class R, int T, int K, int RESID>
-__device__ __noinline__ void levelj_basis(const R* __restrict__ src, R* in, R* ra, R* rd, R* sb, R* __restrict__ dst,
-                                          int M, int y0, int x0, const R* __restrict__ gto, R* __restrict__ gtn,
-                                          int N, const R* __restrict__ rco, IterScalars<R> sc, R w, double* q) {
+__device__ __noinline__ void levelj_basis(R* in, R* ra, R* sb, R* __restrict__ dst, int M, int y0, int x0,
+                                          const R* __restrict__ gto, R* __restrict__ gtn, int N,
+                                          const R* __restrict__ rco, IterScalars<R> sc, R w, double* q,
+                                          const R* __restrict__ next_src, int next_K) {
   auto emit = [&](int, int m, int x, const R* v) {
     R* o = dst + (size_t)(y0 + m) * M + x0 + x;
 #pragma unroll
     for (int t = 0; t < TC<T>::OPI; t++) o[t] = v[t];
   };
-  load_tile_t<R, T>(src, M, y0 - 2 * K + 2, x0 - 2 * K + 2, T + 4 * K - 4, in);
-  __syncthreads();
-  level_tile_t<R, T, K, RESID>(in, 0, ra, sb, M, y0, x0, gto, gtn, N, rco, sc, w, q, emit);
+  auto after_rows = [&] {
+    if (next_src != nullptr)
+      load_tile_t<R, T>(next_src, M, y0 - 2 * next_K + 2, x0 - 2 * next_K + 2, T + 4 * next_K - 4, in);
+  };
+  level_tile_t<R, T, K, RESID>(in, 0, ra, sb, M, y0, x0, gto, gtn, N, rco, sc, w, q, emit, after_rows);
 }
 
 // L2 prefetch of a basis's input tile at a coarser level.
@@ -759,18 +768,23 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_levelj_t(const R* __re
   auto src_of = [&](int k) { return in_img + ((size_t)k * L + band) * MM; };
   auto rc_of = [&](int k) { return coarsest ? (const R*)nullptr : rco + ((size_t)k * L + band) * (MM / 4); };
   if (nd > 0) {
-    prefetch_tile<R, T>(src_of(0), M, ws->K[0], y0, x0);
-    prefetch_level<R, T>(ws->K[0], gto + (size_t)band * NN, rc_of(0), M, N, y0, x0);
+    const int K0 = ws->K[0];
+    load_tile_t<R, T>(src_of(0), M, y0 - 2 * K0 + 2, x0 - 2 * K0 + 2, T + 4 * K0 - 4, in);
+    prefetch_level<R, T>(K0, gto + (size_t)band * NN, rc_of(0), M, N, y0, x0);
   }
   for (int k = 0; k < nd; k++) {
-    if (k + 1 < nd) {
+    const bool more = k + 1 < nd;
+    if (more) {
       prefetch_tile<R, T>(src_of(k + 1), M, ws->K[k + 1], y0, x0);
       prefetch_level<R, T>(ws->K[k + 1], gto + ((size_t)(k + 1) * L + band) * NN, rc_of(k + 1), M, N, y0, x0);
     }
+    cp_async_wait_all();  // this basis's tile
+    __syncthreads();
     const size_t gofs = ((size_t)k * L + band) * NN;
     R* dst = out_img + ((size_t)k * L + band) * MM;
-    MF_K_SWITCH(ws->K[k], (levelj_basis<R, T, KK, RESID>(src_of(k), in, ra, rd, sb, dst, M, y0, x0, gto + gofs,
-                                                         gtn + gofs, N, rc_of(k), sc, ws->w[k], q)));
+    MF_K_SWITCH(ws->K[k], (levelj_basis<R, T, KK, RESID>(in, ra, sb, dst, M, y0, x0, gto + gofs, gtn + gofs, N,
+                                                         rc_of(k), sc, ws->w[k], q, more ? src_of(k + 1) : nullptr,
+                                                         more ? ws->K[k + 1] : 0)));
     __syncthreads();
   }
   if (RESID) block_reduce_write<WNT>(q, partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * MF_NQ);
