@@ -76,6 +76,16 @@ template <class R> struct Dft<R, 8> {
   }
 };
 
+// Asynchronous global -> shared copy of one element (cp.async): a thread issues
+// all of its loads of a tile without waiting for any of them.
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src),
+               "n"((int)sizeof(T))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __host__ __device__ constexpr int first_radix(int n) {
   int p = 1;
   while (p * 8 <= n) p *= 8;
@@ -167,8 +177,10 @@ __global__ void __launch_bounds__(FFT_NT) k_rows_fwd(const R* __restrict__ in, c
   const cx<R>* src = reinterpret_cast<const cx<R>*>(in);
   for (int e = threadIdx.x; e < ROWS * n; e += FFT_NT) {
     const int r = e / n, m = e % n;
-    buf[padded<PAD>(e)] = (row0 + r < rows) ? src[(size_t)(row0 + r) * n + m] : mk<R>(0, 0);
+    if (row0 + r < rows) cp_async_elem(buf + padded<PAD>(e), src + (size_t)(row0 + r) * n + m);
+    else buf[padded<PAD>(e)] = mk<R>(0, 0);
   }
+  cp_async_wait_all();
   __syncthreads();
   fft_all<R, n, 1, ROWS, FFT_NT, n, 1, false, 2, PAD>(buf, tw);
   for (int e = threadIdx.x; e < ROWS * n; e += FFT_NT) {
@@ -204,8 +216,10 @@ __global__ void __launch_bounds__(FFT_NT) k_rows_inv(const cx<R>* __restrict__ i
   const int row0 = blockIdx.x * ROWS;
   for (int e = threadIdx.x; e < ROWS * n; e += FFT_NT) {
     const int r = e / n, m = e % n;
-    buf[padded<PAD>(e)] = (row0 + r < rows) ? in[(size_t)(row0 + r) * n + m] : mk<R>(0, 0);
+    if (row0 + r < rows) cp_async_elem(buf + padded<PAD>(e), in + (size_t)(row0 + r) * n + m);
+    else buf[padded<PAD>(e)] = mk<R>(0, 0);
   }
+  cp_async_wait_all();
   __syncthreads();
   cx<R> z[EPT];
 #pragma unroll
@@ -298,8 +312,9 @@ __global__ void __launch_bounds__(COLS_NT, 2) k_cols(cx<R>* __restrict__ work, c
   cx<R>* base = work + (size_t)band * N * n + kx0;
   for (int e = threadIdx.x; e < EL; e += COLS_NT) {
     const int ky = e / SW, c = e % SW;
-    buf[e] = base[(size_t)ky * n + c];
+    cp_async_elem(buf + e, base + (size_t)ky * n + c);
   }
+  cp_async_wait_all();
   __syncthreads();
   fft_all<R, N, 1, SW, COLS_NT, 1, SW, true, 1>(buf, tw);
 

@@ -7,8 +7,8 @@
 // is dropped).
 //
 // One CTA = 128 pixels = the M dimension of the MMA; after tcgen05.ld each
-// thread holds half of one pixel's spectrum for the pointwise updates (warps
-// w and w + 4 read the same tensor-memory lanes).
+// thread holds a part of one pixel's spectrum for the pointwise updates (warps
+// w, w + 4, ... read the same tensor-memory lanes, 32 (w mod 4) onwards).
 // Operand layout in shared memory: no swizzle, K-major core matrices of
 // 8 rows x 16 bytes; element (r, k) of an R x K operand sits at byte
 // (r / 8) SBO + (k / 8) LBO + (r % 8) 16 + (k % 8) 2 with LBO = 128 and
@@ -29,7 +29,12 @@ namespace mf {
 namespace {
 
 constexpr int TC_M = 128;       // pixels per CTA (MMA M)
-constexpr int TC_NT = 256;      // threads per CTA: two per pixel, each on half of the spectral axis
+// Threads per pixel: four (each on a quarter of the spectral axis) when a
+// quarter is a whole number of 8-column tensor-memory loads, else two.
+template <int LP> struct TcCfg {
+  static constexpr int NPART = ((LP / 4) % 8 == 0) ? 4 : 2;
+  static constexpr int NT = TC_M * NPART;  // threads per CTA
+};
 constexpr int TC_TMEM_COLS = 64;
 constexpr long long TC_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
@@ -150,7 +155,7 @@ __device__ __forceinline__ uint32_t seg_off(int r, int k0) {
 }
 
 template <int LP, int RESID>
-__global__ void __launch_bounds__(TC_NT, 2) k_spectral_tc(const float* __restrict__ X, float* __restrict__ GP,
+__global__ void __launch_bounds__(TcCfg<LP>::NT, 2) k_spectral_tc(const float* __restrict__ X, float* __restrict__ GP,
                                                            float* __restrict__ Sd, float* __restrict__ GV,
                                                            float* __restrict__ GSd, float* __restrict__ b,
                                                            const uint16_t* __restrict__ bmats, int NN, int L,
@@ -169,8 +174,9 @@ __global__ void __launch_bounds__(TC_NT, 2) k_spectral_tc(const float* __restric
 
   const int tid = threadIdx.x, warp = tid >> 5;
   const int row = tid & (TC_M - 1);     // pixel within the tile = tensor-memory lane
-  const int half = tid / TC_M;          // which half of the bands / frequencies
-  constexpr int HL = LP / 2;            // bands or frequencies per thread (a multiple of 8)
+  constexpr int NT = TcCfg<LP>::NT;
+  const int half = tid / TC_M;          // which part of the bands / frequencies
+  constexpr int HL = LP / TcCfg<LP>::NPART;  // bands or frequencies per thread (a multiple of 8)
   const int p = blockIdx.x * TC_M + row;
 
   if (warp == 0) {
@@ -195,7 +201,7 @@ __global__ void __launch_bounds__(TC_NT, 2) k_spectral_tc(const float* __restric
     // segment, so the later phases find them in L2 instead of waiting on HBM.
     {
       const size_t p0 = (size_t)blockIdx.x * TC_M;
-      for (int e = tid; e < 4 * L * (TC_M / 32); e += TC_NT) {
+      for (int e = tid; e < 4 * L * (TC_M / 32); e += NT) {
         const int seg = e % (TC_M / 32), rest = e / (TC_M / 32);
         const int l = rest % L, a = rest / L;
         const float* base = a == 0 ? Sd : a == 1 ? GV : a == 2 ? GSd : GP;
@@ -206,7 +212,7 @@ __global__ void __launch_bounds__(TC_NT, 2) k_spectral_tc(const float* __restric
       // the DCT operands (L2-resident, shared by every CTA)
       const uint4* src = reinterpret_cast<const uint4*>(bmats);
       uint4* dst = reinterpret_cast<uint4*>(B1hi);
-      for (int e = tid; e < 4 * LP * LP / 8; e += TC_NT) dst[e] = src[e];
+      for (int e = tid; e < 4 * LP * LP / 8; e += NT) dst[e] = src[e];
     }
 #pragma unroll
     for (int c0 = 0; c0 < HL; c0 += 8) {
@@ -324,7 +330,7 @@ __global__ void __launch_bounds__(TC_NT, 2) k_spectral_tc(const float* __restric
   tc_fence_before();
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
-  if (RESID) block_reduce_write<TC_NT>(q, partials + (size_t)blockIdx.x * MF_NQ);
+  if (RESID) block_reduce_write<NT>(q, partials + (size_t)blockIdx.x * MF_NQ);
 }
 
 template <int LP>
@@ -338,11 +344,11 @@ cudaError_t spectral_tc_lp(const float* X, float* GP, float* Sd, float* GV, floa
   if (resid) {
     e = cudaFuncSetAttribute(k_spectral_tc<LP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_spectral_tc<LP, 1><<<blocks, TC_NT, sm, s>>>(X, GP, Sd, GV, GSd, b, bmats, NN, L, sc, partials, err);
+    k_spectral_tc<LP, 1><<<blocks, TcCfg<LP>::NT, sm, s>>>(X, GP, Sd, GV, GSd, b, bmats, NN, L, sc, partials, err);
   } else {
     e = cudaFuncSetAttribute(k_spectral_tc<LP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_spectral_tc<LP, 0><<<blocks, TC_NT, sm, s>>>(X, GP, Sd, GV, GSd, b, bmats, NN, L, sc, partials, err);
+    k_spectral_tc<LP, 0><<<blocks, TcCfg<LP>::NT, sm, s>>>(X, GP, Sd, GV, GSd, b, bmats, NN, L, sc, partials, err);
   }
   return cudaGetLastError();
 }
