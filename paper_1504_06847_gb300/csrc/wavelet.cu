@@ -744,8 +744,9 @@ __device__ __forceinline__ void prefetch_tile(const R* src, int M, int K, int y0
   }
 }
 
-// Coarser level j >= 2 (M = N / 2^(j-1)): every basis in one CTA, in turn, with
-// the next basis's tile and coefficients prefetched into L2; writes R_{j-1}.
+// Coarser level j >= 2 (M = N / 2^(j-1)): the bases of one group (blockIdx.z;
+// one group unless the grid would be too small to fill the GPU) in one CTA, in
+// turn, with the next basis's tile and coefficients prefetched; writes R_{j-1}.
 template <class R, int T, int RESID>
 __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_levelj_t(const R* __restrict__ in_img,
                                                                   R* __restrict__ out_img,
@@ -764,16 +765,19 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_levelj_t(const R* __re
 #pragma unroll
   for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
   q[Q_XMIN] = 1e300;
-  const int nd = ws->nd;
+  // this CTA's bases: group blockIdx.z of gridDim.z equal groups
+  const int per = (ws->nd + gridDim.z - 1) / gridDim.z;
+  const int kb = blockIdx.z * per;
+  const int ke = kb + per < ws->nd ? kb + per : ws->nd;
   auto src_of = [&](int k) { return in_img + ((size_t)k * L + band) * MM; };
   auto rc_of = [&](int k) { return coarsest ? (const R*)nullptr : rco + ((size_t)k * L + band) * (MM / 4); };
-  if (nd > 0) {
-    const int K0 = ws->K[0];
-    load_tile_t<R, T>(src_of(0), M, y0 - 2 * K0 + 2, x0 - 2 * K0 + 2, T + 4 * K0 - 4, in);
-    prefetch_level<R, T>(K0, gto + (size_t)band * NN, rc_of(0), M, N, y0, x0);
+  if (kb < ke) {
+    const int K0 = ws->K[kb];
+    load_tile_t<R, T>(src_of(kb), M, y0 - 2 * K0 + 2, x0 - 2 * K0 + 2, T + 4 * K0 - 4, in);
+    prefetch_level<R, T>(K0, gto + ((size_t)kb * L + band) * NN, rc_of(kb), M, N, y0, x0);
   }
-  for (int k = 0; k < nd; k++) {
-    const bool more = k + 1 < nd;
+  for (int k = kb; k < ke; k++) {
+    const bool more = k + 1 < ke;
     if (more) {
       prefetch_tile<R, T>(src_of(k + 1), M, ws->K[k + 1], y0, x0);
       prefetch_level<R, T>(ws->K[k + 1], gto + ((size_t)(k + 1) * L + band) * NN, rc_of(k + 1), M, N, y0, x0);
@@ -787,7 +791,9 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_levelj_t(const R* __re
                                                          more ? ws->K[k + 1] : 0)));
     __syncthreads();
   }
-  if (RESID) block_reduce_write<WNT>(q, partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * MF_NQ);
+  if (RESID)
+    block_reduce_write<WNT>(
+        q, partials + (((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * MF_NQ);
 }
 
 // Low-low analysis: LL_j (M/2 x M/2) of the M x M input, for one basis per CTA
@@ -1072,11 +1078,20 @@ static int level_tile_edge(int M, int pref) {
   return M < WT ? M : WT;
 }
 
+// Basis groups of a coarser level with T = 64 / 32 tiles: enough CTAs for about
+// eight waves of two per SM, at most one group per basis.
+static int levelj_groups(int tiles, int L, int nd) {
+  const int target = 152 * 2 * 8;
+  const int g = (target + tiles * L - 1) / (tiles * L);
+  return g < 1 ? 1 : (g > nd ? nd : g);
+}
+
 template <class R>
 int wav_level_blocks(int M, int L, int nd, int pref) {
   const int T = level_tile_edge(M, pref);
   const int tiles = (M / T) * (M / T);
-  return T >= 32 ? tiles * L : tiles * L * nd;  // the T = 64 / 32 kernels loop over bases in a CTA
+  // the T = 64 / 32 kernels loop over a group of bases in a CTA (level 1: all, nd = 1 here)
+  return T >= 32 ? tiles * L * levelj_groups(tiles, L, nd) : tiles * L * nd;
 }
 
 template <class R>
@@ -1115,7 +1130,7 @@ static cudaError_t launch_level_t(const R* in, const R* rcoarse, R* out, const R
     return launch_k<R>(k_wav_level1_t<R, T, 0>, grid, sm1, s, in, out, gt_old, gt_new, rcoarse, N, L, coarsest, ws,
                        sc, partials);
   }
-  dim3 grid(tiles, L);
+  dim3 grid(tiles, L, levelj_groups(tiles, L, nd));
   const size_t sm = sizeof(R) * TC<T>::SMEM;
   if (resid)
     return launch_k<R>(k_wav_levelj_t<R, T, 1>, grid, sm, s, in, out, gt_old, gt_new, rcoarse, N, M, L, coarsest, ws,
