@@ -35,6 +35,10 @@ constexpr int CWM = WT / 2 + MF_MAX_K - 1;   // coefficient tile edge
 constexpr int OPT = WT * WT / WNT;           // output pixels per thread
 constexpr int LT = 32;                       // output tile edge of the low-low kernel
 constexpr int LIM = 2 * LT + 2 * MF_MAX_K - 2;
+constexpr int LIMP = LIM + 1;                // pitch (in pairs) of the row-pair layout of the low-low input
+constexpr int LTP = LT + 2;                  // pitch of the packed low-low row-analysis buffer
+constexpr int LL_IN = (LIM / 2) * LIMP * 2 > LIM * LIM ? (LIM / 2) * LIMP * 2 : LIM * LIM;  // input region
+constexpr int LL_A = LIM * LTP;              // row-analysis region (>= LIM * LT)
 
 // Daubechies taps by half-length K (the same numbers for every plan):
 // low-pass h_n and high-pass g_n = (-1)^n h_{2K-1-n}.  With K and n known at
@@ -860,19 +864,108 @@ __device__ __forceinline__ void ll_tile(const R* in, R* a, int TO, const R* __re
   __syncthreads();
 }
 
+// Loads an H x H tile (H even) of an M x M image (periodic) in the row-pair
+// layout of the packed low-low analysis: element (r, c) is member r % 2 of
+// pair (r / 2) LIMP + c.
+template <class R>
+__device__ __forceinline__ void load_tile_rowpairs(const R* __restrict__ img, int M, int r0, int c0, int H, R* dst) {
+  for (int e = threadIdx.x; e < H * H; e += WNT) {
+    const int r = e / H, c = e % H;
+    cp_async_elem(dst + (((r >> 1) * LIMP + c) << 1) + (r & 1),
+                  img + (size_t)((r0 + r) & (M - 1)) * M + ((c0 + c) & (M - 1)));
+  }
+  cp_async_wait_all();
+}
+
+// Low-low analysis of one LT x LT output tile on packed pairs: the row pass
+// filters two input rows at once ({row 2p, row 2p + 1} pairs), the column pass
+// two adjacent columns at once; one fma.rn.f32x2 per tap.
+template <class R, int K>
+__device__ __forceinline__ void ll_tile_packed(const R* in, R* a, R* __restrict__ dst, int Mo, int oy, int ox) {
+  typedef typename V2<R>::T P;
+  constexpr int F = 2 * K;
+  constexpr int IH = 2 * LT + F - 2;  // input rows and columns used (even)
+  constexpr int RO = 4;               // row pass: outputs per item
+  constexpr int NVR = 2 * RO - 2 + F;
+  constexpr int RC = 2;               // column pass: output rows per item
+  constexpr int NVC = 2 * RC - 2 + F;
+  const P* pin = reinterpret_cast<const P*>(in);
+  // rows: row pair p, low-pass outputs RO j..RO j+RO-1; consecutive threads take consecutive pairs
+  for (int it = threadIdx.x; it < (IH / 2) * (LT / RO); it += WNT) {
+    const int p = it % (IH / 2), j = it / (IH / 2);
+    const P* src = pin + p * LIMP + 2 * RO * j;
+    P v[NVR];
+#pragma unroll
+    for (int t = 0; t < NVR; t++) v[t] = src[t];
+    P o[RO];
+#pragma unroll
+    for (int c = 0; c < RO; c++) {
+      P acc = mk2((R)0, (R)0);
+#pragma unroll
+      for (int n = 0; n < F; n++) acc = fma2(Taps2<R>::hh(K, n), v[2 * c + n], acc);
+      o[c] = acc;  // {row 2p, row 2p + 1} of output column RO j + c
+    }
+    P* d0 = reinterpret_cast<P*>(a + (2 * p) * LTP + RO * j);
+    P* d1 = reinterpret_cast<P*>(a + (2 * p + 1) * LTP + RO * j);
+#pragma unroll
+    for (int c = 0; c < RO; c += 2) {
+      d0[c / 2] = mk2(o[c].x, o[c + 1].x);
+      d1[c / 2] = mk2(o[c].y, o[c + 1].y);
+    }
+  }
+  __syncthreads();
+  // columns: column pair q, output rows RC j..RC j+RC-1; consecutive threads take consecutive pairs
+  for (int it = threadIdx.x; it < (LT / 2) * (LT / RC); it += WNT) {
+    const int q = it % (LT / 2), j = it / (LT / 2);
+    const P* col = reinterpret_cast<const P*>(a + 2 * RC * j * LTP + 2 * q);
+    P v[NVC];
+#pragma unroll
+    for (int t = 0; t < NVC; t++) v[t] = col[t * (LTP / 2)];
+#pragma unroll
+    for (int i = 0; i < RC; i++) {
+      P acc = mk2((R)0, (R)0);
+#pragma unroll
+      for (int n = 0; n < F; n++) acc = fma2(Taps2<R>::hh(K, n), v[2 * i + n], acc);
+      *reinterpret_cast<P*>(dst + (size_t)(oy + RC * j + i) * Mo + ox + 2 * q) = acc;
+    }
+  }
+  __syncthreads();
+}
+
 template <class R>
 __global__ void __launch_bounds__(WNT) k_wav_ll(const R* __restrict__ in_img, size_t in_band_stride,
                                                  size_t in_basis_stride, R* __restrict__ out, int M, int L,
                                                  const WavSet<R>* __restrict__ ws) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* in = reinterpret_cast<R*>(smem_raw);
-  R* a = in + LIM * LIM;
+  R* a = in + LL_IN;
   const int Mo = M / 2;
   const int TO = Mo < LT ? Mo : LT;
   const int tpd = Mo / TO;
   const int band = blockIdx.y;
   const int oy = (blockIdx.x / tpd) * TO, ox = (blockIdx.x % tpd) * TO;
   const size_t MMo = (size_t)Mo * Mo;
+  if (TO == LT) {
+    // full LT x LT tiles: the packed form
+    if (in_basis_stride == 0) {
+      load_tile_rowpairs<R>(in_img + band * in_band_stride, M, 2 * oy, 2 * ox, LIM, in);
+      __syncthreads();
+      for (int k = 0; k < ws->nd; k++) {
+        R* dst = out + ((size_t)k * L + band) * MMo;
+        MF_K_SWITCH(ws->K[k], (ll_tile_packed<R, KK>(in, a, dst, Mo, oy, ox)));
+      }
+    } else {
+      const int k = blockIdx.z;
+      const R* src = in_img + band * in_band_stride + k * in_basis_stride;
+      R* dst = out + ((size_t)k * L + band) * MMo;
+      MF_K_SWITCH(ws->K[k], {
+        load_tile_rowpairs<R>(src, M, 2 * oy, 2 * ox, 2 * LT + 2 * KK - 2, in);
+        __syncthreads();
+        ll_tile_packed<R, KK>(in, a, dst, Mo, oy, ox);
+      });
+    }
+    return;
+  }
   if (in_basis_stride == 0) {
     const R* src = in_img + band * in_band_stride;
     load_tile<R>(src, M, 2 * oy, 2 * ox, 2 * TO + 2 * MF_MAX_K - 2, 2 * TO + 2 * MF_MAX_K - 2, in, LIM);
@@ -1100,7 +1193,7 @@ cudaError_t launch_wav_ll(const R* in, size_t in_band_stride, size_t in_basis_st
   const int Mo = M / 2;
   const int TO = Mo < LT ? Mo : LT;
   const int tiles = (Mo / TO) * (Mo / TO);
-  const size_t sm = sizeof(R) * (LIM * LIM + LIM * LT);
+  const size_t sm = sizeof(R) * (LL_IN + LL_A);
   cudaError_t e = cudaFuncSetAttribute(k_wav_ll<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   dim3 grid(tiles, L, in_basis_stride == 0 ? 1 : nd);
