@@ -280,14 +280,14 @@ struct ColFilter {
   const cx<R>* hh;
   const cx<R>* yh;
   // X^ of one bin from B^ = Z; MODE 2 adds wfit |F(y) - N^2 h X^|^2 to fit
-  __device__ __forceinline__ cx<R> apply(cx<R> Z, size_t o, R N2, double& fit, double wfit) const {
+  __device__ __forceinline__ cx<R> apply(cx<R> Z, size_t o, R N2, R& fit, R wfit) const {
     cx<R> Xh;
     if (MODE == 3) Xh = cscale<R>(cmul<R>(hh[o], Z), (R)1 / N2);
     else if (MODE == 4) Xh = cscale<R>(Z, gg[o]);
     else Xh = cadd<R>(cc[o], cscale<R>(Z, gg[o]));
     if (MODE == 2) {
       const cx<R> r = csub<R>(yh[o], cscale<R>(cmul<R>(hh[o], Xh), N2));
-      fit += wfit * ((double)r.x * r.x + (double)r.y * r.y);
+      fit = fma(wfit, r.x * r.x + r.y * r.y, fit);
     }
     return Xh;
   }
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(COLS_NT, 2) k_cols(cx<R>* __restrict__ work, c
     const R N2 = (R)N * (R)N;
     const ColFilter<R, MODE> fm{cc, gg, hh, yh};
     const ColFilter<R, MODE> fn{cc_nyq, gg_nyq, hh_nyq, yh_nyq};
-    double fit = 0.0;
+    R fit = 0;  // this thread's 16 or so bins in the cube's precision; FP64 from the block sum on
     auto unpack_row = [&](int ky, cx<R> Z, cx<R> Zmir) {
       // row ky of column 0 from Z = buf[ky] and Zmir = buf[(N - ky) mod N]
       const cx<R> Zm = cconj<R>(Zmir);
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(COLS_NT, 2) k_cols(cx<R>* __restrict__ work, c
       const cx<R> D = csub<R>(Z, Zm);
       const cx<R> B = mk<R>((R)0.5 * D.y, (R)-0.5 * D.x);
       const size_t o = ((size_t)band * N + ky) * n, on = (size_t)band * N + ky;
-      const cx<R> Ax = fm.apply(A, o, N2, fit, 1.0), Bx = fn.apply(B, on, N2, fit, 1.0);
+      const cx<R> Ax = fm.apply(A, o, N2, fit, (R)1), Bx = fn.apply(B, on, N2, fit, (R)1);
       return cconj<R>(mk<R>(Ax.x - Bx.y, Ax.y + Bx.x));  // conj(A' + i B')
     };
     for (int e = threadIdx.x; e < EL; e += COLS_NT) {
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(COLS_NT, 2) k_cols(cx<R>* __restrict__ work, c
         buf[ky * SW] = v;
       } else {
         const size_t o = ((size_t)band * N + ky) * n + kx;
-        buf[e] = cconj<R>(fm.apply(buf[e], o, N2, fit, 2.0));
+        buf[e] = cconj<R>(fm.apply(buf[e], o, N2, fit, (R)2));
       }
     }
     __syncthreads();
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(COLS_NT, 2) k_cols(cx<R>* __restrict__ work, c
 #pragma unroll
       for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
       q[Q_XMIN] = 1e300;
-      q[Q_FIT] = 0.5 * fit / ((double)N * (double)N);
+      q[Q_FIT] = 0.5 * (double)fit / ((double)N * (double)N);
       block_reduce_write<COLS_NT>(q, partials + (size_t)blockIdx.x * MF_NQ);
     }
   }

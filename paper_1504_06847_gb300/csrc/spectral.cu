@@ -97,12 +97,10 @@ __global__ void __launch_bounds__(SP_NT) k_spectral(const R* __restrict__ X, R* 
       for (int c = 0; c < 4; c++) acc[a][c] = fma(c4[a], x4[c], acc[a][c]);
   }
 
-  double q[Q_COUNT];
-  if (RESID) {
-#pragma unroll
-    for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
-    q[Q_XMIN] = 1e300;
-  }
+  // residual terms of this thread's 16 voxels, summed in the cube's precision and
+  // folded into the FP64 partial rows once (FP64 arithmetic per voxel is slow)
+  R r_dgv = 0, r_dgs = 0, r_l1 = 0, r_dgp = 0, r_x2 = 0, r_xmin = (R)3.0e38;
+  bool r_bad = false;
 
   // DCT-domain part of steps IV, V and VI
   R u[4][4];
@@ -123,11 +121,11 @@ __global__ void __launch_bounds__(SP_NT) k_spectral(const R* __restrict__ X, R* 
         const R gvn = gv[c] + sc.rho_V * (v - sn);
         const R gsn = gs[c] + sc.rho_S * (sn - xh);
         if (RESID) {
-          const double dv = (double)gvn - (double)gv[c], ds = (double)gsn - (double)gs[c];
-          q[Q_DGV] += dv * dv;
-          q[Q_DGS] += ds * ds;
-          q[Q_L1NU] += fabs((double)xh);
-          if (!finite_<R>(gvn) || !finite_<R>(gsn)) q[Q_NONFIN] += 1.0;
+          const R dv = gvn - gv[c], ds = gsn - gs[c];
+          r_dgv = fma(dv, dv, r_dgv);
+          r_dgs = fma(ds, ds, r_dgs);
+          r_l1 += fabs(xh);
+          r_bad |= !finite_<R>(gvn) || !finite_<R>(gsn);
         }
         s[c] = sn;
         gv[c] = gvn;
@@ -175,11 +173,11 @@ __global__ void __launch_bounds__(SP_NT) k_spectral(const R* __restrict__ X, R* 
         const R pp = pt > (R)0 ? pt : (R)0;
         const R gpn = gp[c] + sc.rho_P * (pp - x);
         if (RESID) {
-          const double d = (double)gpn - (double)gp[c];
-          q[Q_DGP] += d * d;
-          q[Q_X2] += (double)x * (double)x;
-          q[Q_XMIN] = fmin(q[Q_XMIN], (double)x);
-          if (!finite_<R>(x) || !finite_<R>(gpn)) q[Q_NONFIN] += 1.0;
+          const R d = gpn - gp[c];
+          r_dgp = fma(d, d, r_dgp);
+          r_x2 = fma(x, x, r_x2);
+          r_xmin = x < r_xmin ? x : r_xmin;
+          r_bad |= !finite_<R>(x) || !finite_<R>(gpn);
         }
         gp[c] = gpn;
         bo[c] = gpn + sc.rho_P * pp + bs[a][c];
@@ -188,7 +186,19 @@ __global__ void __launch_bounds__(SP_NT) k_spectral(const R* __restrict__ X, R* 
       V4<R>::st(b + o, bo);
     }
   }
-  if (RESID) block_reduce_write<SP_NT>(q, partials + (size_t)blockIdx.x * MF_NQ);
+  if (RESID) {
+    double q[Q_COUNT];
+#pragma unroll
+    for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
+    q[Q_DGV] = (double)r_dgv;
+    q[Q_DGS] = (double)r_dgs;
+    q[Q_L1NU] = (double)r_l1;
+    q[Q_DGP] = (double)r_dgp;
+    q[Q_X2] = (double)r_x2;
+    q[Q_XMIN] = r_xmin < (R)3.0e38 ? (double)r_xmin : 1e300;
+    q[Q_NONFIN] = r_bad ? 1.0 : 0.0;
+    block_reduce_write<SP_NT>(q, partials + (size_t)blockIdx.x * MF_NQ);
+  }
 }
 
 // Adjoint of the spectral step (steps II, IV, V and their duals, and the

@@ -240,12 +240,10 @@ __global__ void __launch_bounds__(TcCfg<LP>::NT, 2) k_spectral_tc(const float* _
   bool ok = mbar_wait(mbar, 0);
   tc_fence_after();
 
-  double q[Q_COUNT];
-  if (RESID) {
-#pragma unroll
-    for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
-    q[Q_XMIN] = 1e300;
-  }
+  // residual terms of this thread's voxels in FP32, folded into the FP64
+  // partial rows once (FP64 arithmetic per voxel is slow)
+  float r_dgv = 0.f, r_dgs = 0.f, r_l1 = 0.f, r_dgp = 0.f, r_x2 = 0.f, r_xmin = 3.0e38f;
+  bool r_bad = false;
 
   if (ok) {
     // DCT-domain part of steps IV, V, VI; U = Gamma_S + rho_S S becomes the next A operand
@@ -269,11 +267,11 @@ __global__ void __launch_bounds__(TcCfg<LP>::NT, 2) k_spectral_tc(const float* _
           GSd[o] = gsn;
           u[t] = gsn + sc.rho_S * sn;
           if (RESID) {
-            const double dv = (double)gvn - gv, ds = (double)gsn - gs;
-            q[Q_DGV] += dv * dv;
-            q[Q_DGS] += ds * ds;
-            q[Q_L1NU] += fabs((double)xh[t]);
-            if (!isfinite(gvn) || !isfinite(gsn)) q[Q_NONFIN] += 1.0;
+            const float dv = gvn - gv, ds = gsn - gs;
+            r_dgv = fmaf(dv, dv, r_dgv);
+            r_dgs = fmaf(ds, ds, r_dgs);
+            r_l1 += fabsf(xh[t]);
+            r_bad |= !isfinite(gvn) || !isfinite(gsn);
           }
         }
       }
@@ -315,11 +313,11 @@ __global__ void __launch_bounds__(TcCfg<LP>::NT, 2) k_spectral_tc(const float* _
           GP[o] = gpn;
           b[o] = gpn + sc.rho_P * pp + bs[t];
           if (RESID) {
-            const double d = (double)gpn - gp;
-            q[Q_DGP] += d * d;
-            q[Q_X2] += (double)x * x;
-            q[Q_XMIN] = fmin(q[Q_XMIN], (double)x);
-            if (!isfinite(x) || !isfinite(gpn)) q[Q_NONFIN] += 1.0;
+            const float d = gpn - gp;
+            r_dgp = fmaf(d, d, r_dgp);
+            r_x2 = fmaf(x, x, r_x2);
+            r_xmin = fminf(r_xmin, x);
+            r_bad |= !isfinite(x) || !isfinite(gpn);
           }
         }
       }
@@ -330,7 +328,19 @@ __global__ void __launch_bounds__(TcCfg<LP>::NT, 2) k_spectral_tc(const float* _
   tc_fence_before();
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
-  if (RESID) block_reduce_write<NT>(q, partials + (size_t)blockIdx.x * MF_NQ);
+  if (RESID) {
+    double q[Q_COUNT];
+#pragma unroll
+    for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
+    q[Q_DGV] = r_dgv;
+    q[Q_DGS] = r_dgs;
+    q[Q_L1NU] = r_l1;
+    q[Q_DGP] = r_dgp;
+    q[Q_X2] = r_x2;
+    q[Q_XMIN] = r_xmin < 3.0e38f ? (double)r_xmin : 1e300;
+    q[Q_NONFIN] = r_bad ? 1.0 : 0.0;
+    block_reduce_write<NT>(q, partials + (size_t)blockIdx.x * MF_NQ);
+  }
 }
 
 template <int LP>

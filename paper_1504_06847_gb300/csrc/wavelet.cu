@@ -523,16 +523,20 @@ __device__ __forceinline__ void level_tile_t(const R* in, int off, R* rpair, R* 
       P v[NV];
 #pragma unroll
       for (int t = 0; t < NV; t++) v[t] = col[t * B_CP];
+      // residual terms of the item's owned coefficients, in the cube's precision,
+      // folded into the FP64 sums once per item
+      R r_dg = 0, r_l1 = 0;
+      bool r_bad = false;
       auto update = [&](R z, R gam, bool own, int pos) -> R {
         const R tp = soft_w<R>(z - gam * sc.inv_rho_T, sc.tau_T);
         const R gn = gam + sc.rho_T * (tp - z);
         if (own) {
           gtn[pos] = gn;
           if (RESID) {
-            const double dg = (double)gn - (double)gam;
-            q[Q_DGT] += (double)w * dg * dg;
-            q[Q_L1S] += (double)w * fabs((double)z);
-            if (!isfinite(gn)) q[Q_NONFIN] += 1.0;
+            const R dg = gn - gam;
+            r_dg = fma(dg, dg, r_dg);
+            r_l1 += fabs(z);
+            r_bad |= !isfinite(gn);
           }
         }
         return gn + sc.rho_T * tp;
@@ -550,6 +554,11 @@ __device__ __forceinline__ void level_tile_t(const R* in, int off, R* rpair, R* 
         const R tl = rco != nullptr ? gtl[i] : update(lo.x, gtl[i], own, go[i]);
         top[row * B_CP + c] = mk2(tl, update(lo.y, gtr[i], own, go[i] + Mh));
         bot[row * B_CP + c] = mk2(update(hi.x, gbl[i], own, go[i] + MhN), update(hi.y, gbr[i], own, go[i] + MhN + Mh));
+      }
+      if (RESID) {
+        q[Q_DGT] += (double)w * (double)r_dg;
+        q[Q_L1S] += (double)w * (double)r_l1;
+        if (r_bad) q[Q_NONFIN] += 1.0;
       }
     }
   }
