@@ -314,6 +314,21 @@ __global__ void __launch_bounds__(COLS_NT, 2) k_cols(cx<R>* __restrict__ work, c
     const int ky = e / SW, c = e % SW;
     cp_async_elem(buf + e, base + (size_t)ky * n + c);
   }
+  if (MODE != 0) {
+    // L2 prefetch of the strip's filter constants (read after the forward
+    // transform): one line per row of the strip and array
+    const size_t b0 = (size_t)band * N * n + kx0;
+    for (int ky = threadIdx.x; ky < N; ky += COLS_NT) {
+      const size_t o = b0 + (size_t)ky * n;
+      if (MODE == 1 || MODE == 2) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(cc + o));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(gg + o));
+      }
+      if (MODE == 4) asm volatile("prefetch.global.L2 [%0];" ::"l"(gg + o));
+      if (MODE == 2 || MODE == 3) asm volatile("prefetch.global.L2 [%0];" ::"l"(hh + o));
+      if (MODE == 2) asm volatile("prefetch.global.L2 [%0];" ::"l"(yh + o));
+    }
+  }
   cp_async_wait_all();
   __syncthreads();
   fft_all<R, N, 1, SW, COLS_NT, 1, SW, true, 1>(buf, tw);
@@ -350,6 +365,7 @@ __global__ void __launch_bounds__(COLS_NT, 2) k_cols(cx<R>* __restrict__ work, c
       const cx<R> Ax = fm.apply(A, o, N2, fit, (R)1), Bx = fn.apply(B, on, N2, fit, (R)1);
       return cconj<R>(mk<R>(Ax.x - Bx.y, Ax.y + Bx.x));  // conj(A' + i B')
     };
+#pragma unroll 4
     for (int e = threadIdx.x; e < EL; e += COLS_NT) {
       const int ky = e / SW, c = e % SW, kx = kx0 + c;
       if (kx == 0) {
