@@ -878,10 +878,11 @@ __device__ __forceinline__ void ll_tile(const R* in, R* a, int TO, const R* __re
 // pair (r / 2) LIMP + c.
 template <class R>
 __device__ __forceinline__ void load_tile_rowpairs(const R* __restrict__ img, int M, int r0, int c0, int H, R* dst) {
-  for (int e = threadIdx.x; e < H * H; e += WNT) {
-    const int r = e / H, c = e % H;
-    cp_async_elem(dst + (((r >> 1) * LIMP + c) << 1) + (r & 1),
-                  img + (size_t)((r0 + r) & (M - 1)) * M + ((c0 + c) & (M - 1)));
+  // one warp per row, lanes along the row
+  for (int r = threadIdx.x >> 5; r < H; r += WNT / 32) {
+    const R* src = img + (size_t)((r0 + r) & (M - 1)) * M;
+    R* d = dst + (r >> 1) * LIMP * 2 + (r & 1);
+    for (int c = threadIdx.x & 31; c < H; c += 32) cp_async_elem(d + 2 * c, src + ((c0 + c) & (M - 1)));
   }
   cp_async_wait_all();
 }
