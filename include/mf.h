@@ -127,9 +127,12 @@ mf_status mf_batch_iterate(mf_plan* const* plans, const float* const* y_cubes, i
  * writes dL/dy into dL_dy (device [L][N][N]) and dL/dmu_s, dL/dmu_nu, dL/drho
  * into the host doubles (any may be NULL).  Subgradients: the derivative of
  * max(0, t) and of the soft threshold in t is 1 only where the inequality is
- * strict.  Allocates the checkpoints ((5 + nd) cubes per iteration) and
- * (8 + 3 nd) work cubes for the call and synchronises prm->stream before
- * returning; afterwards the plan holds the forward's final state.
+ * strict.  Needs device memory for the checkpoints ((5 + nd) cubes per
+ * iteration) and (7 + 4 nd) work cubes (nd = distinct bases, at most 8): the
+ * plan allocates it on the first call, keeps it for later calls, grows it
+ * when a call needs more and frees it with the plan.  Synchronises
+ * prm->stream before returning; afterwards the plan holds the forward's
+ * final state.
  * Errors: MF_ERR_INVALID, MF_ERR_OOM, MF_ERR_CUDA. */
 mf_status mf_admm_backward(mf_plan* p, const float* y_cube, const mf_params* prm, int n_iter, const float* dL_dX,
                            float* dL_dy, double* dL_dmu_s, double* dL_dmu_nu, double* dL_drho);

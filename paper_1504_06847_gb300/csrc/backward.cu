@@ -64,13 +64,6 @@ unsigned grid_for(size_t n) {
   return (unsigned)(b < 152 * 16 ? (b ? b : 1) : 152 * 16);
 }
 
-struct DevBuf {
-  void* p = nullptr;
-  ~DevBuf() {
-    if (p) cudaFree(p);
-  }
-};
-
 }  // namespace
 
 // Applies Q^-1 (mode 4) or H (mode 3) to src, result in dst (uses the plan's work buffer).
@@ -119,24 +112,40 @@ extern "C" mf_status mf_admm_backward(mf_plan* p, const float* y, const mf_param
 
   // checkpoints: per iteration X_k and the multipliers / S entering it
   const size_t per_ck = (size_t)(5 + nd);  // X, GP, Sd, GV, GSd, GT[nd]
-  DevBuf ck, work;
-  if (cudaMalloc(&ck.p, cb * per_ck * n_iter) != cudaSuccess) {
-    cudaGetLastError();
-    return MF_ERR_OOM;
+  // cotangents and scratch: Xbar, bbar, ybar, GPc, Sc, GVc, GSc, tmp[nd] (the wavelet
+  // transforms of all bases at once; its first cube also serves the filters), GTc[nd],
+  // coefZ[nd], coefU[nd]
+  const size_t nwork = 7 + 4 * (size_t)nd;
+  const size_t need = cb * (per_ck * n_iter + nwork);
+  if (need > p->bwd_bytes) {
+    // the plan keeps this memory for later calls; it grows it when a call needs more
+    if (p->bwd_buf) {
+      cudaError_t fe = cudaStreamSynchronize(s);
+      if (fe == cudaSuccess) fe = cudaFree(p->bwd_buf);
+      p->bwd_buf = nullptr;
+      p->bwd_bytes = 0;
+      if (fe != cudaSuccess) {
+        cudaGetLastError();
+        p->status = MF_ERR_CUDA;
+        return MF_ERR_CUDA;
+      }
+    }
+    if (cudaMalloc(&p->bwd_buf, need) != cudaSuccess) {
+      cudaGetLastError();
+      p->bwd_buf = nullptr;
+      return MF_ERR_OOM;
+    }
+    p->bwd_bytes = need;
   }
-  // cotangents and scratch: Xbar, bbar, ybar, tmp, GPc, Sc, GVc, GSc, GTc[nd], coefZ[nd], coefU[nd]
-  const size_t nwork = 8 + 3 * (size_t)nd;
-  if (cudaMalloc(&work.p, cb * nwork) != cudaSuccess) {
-    cudaGetLastError();
-    return MF_ERR_OOM;
-  }
-  float* W = (float*)work.p;
-  float *Xbar = W, *bbar = W + V, *ybar = W + 2 * V, *tmp = W + 3 * V;
-  float *GPc = W + 4 * V, *Sc = W + 5 * V, *GVc = W + 6 * V, *GSc = W + 7 * V;
-  float* GTc = W + 8 * V;
+  float* ckp = (float*)p->bwd_buf;
+  float* W = ckp + per_ck * n_iter * V;
+  float *Xbar = W, *bbar = W + V, *ybar = W + 2 * V;
+  float *GPc = W + 3 * V, *Sc = W + 4 * V, *GVc = W + 5 * V, *GSc = W + 6 * V;
+  float* tmp = W + 7 * V;
+  float* GTc = tmp + nd * V;
   float* coefZ = GTc + nd * V;
   float* coefU = coefZ + nd * V;
-  auto slot = [&](int k, int which) { return (float*)ck.p + ((size_t)k * per_ck + which) * V; };
+  auto slot = [&](int k, int which) { return ckp + ((size_t)k * per_ck + which) * V; };
 
   cudaError_t e = cudaSuccess;
   // forward with checkpoints (iteration k = 0..n_iter-1 checkpoints X_{k+1} and its input state)

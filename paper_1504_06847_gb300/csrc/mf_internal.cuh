@@ -66,6 +66,9 @@ struct mf_plan {
   int N, L, dbl;
   size_t esz;        // sizeof real type
   size_t cube;       // N * N * L elements
+  // reverse-pass checkpoints and work arrays, kept between calls (grown on demand)
+  void* bwd_buf = nullptr;
+  size_t bwd_bytes = 0;
   // ADMM state and work arrays (real type, [L][N][N] unless noted)
   void* X;
   void* b;

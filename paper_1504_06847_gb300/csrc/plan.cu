@@ -93,9 +93,11 @@ struct Alloc {
 void free_plan_memory(mf_plan* p) {
   void* ptrs[] = {p->X, p->b, p->GP, p->Sd, p->GV, p->GSd, p->GT[0], p->GT[1], p->work, p->hhat, p->hhat_nyq,
                   p->yhat, p->yhat_nyq, p->cc, p->cc_nyq, p->gg, p->gg_nyq, p->tw, p->dctC, p->scratch,
-                  p->partials, p->sums, p->wset, p->dct_tc, p->err};
+                  p->partials, p->sums, p->wset, p->dct_tc, p->err, p->bwd_buf};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  p->bwd_buf = nullptr;
+  p->bwd_bytes = 0;
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   p->ev_pool.clear();
 }
@@ -615,7 +617,7 @@ void mf_plan_destroy(mf_plan* p) {
   delete p;
 }
 
-size_t mf_plan_device_bytes(const mf_plan* p) { return p ? p->total_bytes : 0; }
+size_t mf_plan_device_bytes(const mf_plan* p) { return p ? p->total_bytes + p->bwd_bytes : 0; }
 
 mf_status mf_admm_iterate(mf_plan* p, const float* y, const mf_params* prm, int n_iter) {
   return iterate<float>(p, y, prm, n_iter);

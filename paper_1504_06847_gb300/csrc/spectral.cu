@@ -265,7 +265,9 @@ __global__ void __launch_bounds__(SP_NT) k_spectral_bwd(const R* __restrict__ X,
         gh[a][c] = fma(c4[a], b4[c], gh[a][c]);
       }
   }
-  double dmunu = 0.0, drho = 0.0;
+  // each voxel's gradient terms in the cube's precision, summed in FP64 (one add per
+  // term: FP64 multiplies per voxel are slow)
+  double dmunu_r = 0, drho_r = 0;
   const R irho = (R)1 / rho, tauv = mu_nu / rho;
   R xhb[4][4];
 #pragma unroll
@@ -294,15 +296,15 @@ __global__ void __launch_bounds__(SP_NT) k_spectral_bwd(const R* __restrict__ X,
         const R A1 = gsc[c] + gh[a][c];         // Gamma_S^'
         const R A2 = sc_[c] + rho * gh[a][c];   // S^' (outside the duals)
         const R C1 = gvc[c];                    // Gamma_V'
-        drho += (double)gh[a][c] * sn;
+        drho_r += (double)(gh[a][c] * sn);
         const R Sb = A2 - rho * C1 + rho * A1;  // total on S^'
         R Vb = rho * C1 + (R)0.5 * Sb;
-        drho += (double)C1 * (v - sn) + (double)A1 * (sn - xh[a][c]) +
-                (double)Sb * ((v + xh[a][c]) * ((R)0.5 * irho) - sn * irho);
+        drho_r += (double)(C1 * (v - sn) + A1 * (sn - xh[a][c]) +
+                Sb * ((v + xh[a][c]) * ((R)0.5 * irho) - sn * irho));
         const R vtb = mv ? Vb : (R)0;
         const R taub = mv ? -sv * Vb : (R)0;
-        dmunu += (double)taub * irho;
-        drho += -(double)taub * mu_nu * irho * irho + (double)vtb * gv[c] * irho * irho;
+        dmunu_r += (double)(taub * irho);
+        drho_r += (double)((vtb * gv[c] - taub * mu_nu) * irho * irho);
         sc_[c] = vtb;
         gvc[c] = C1 + (R)0.5 * Sb * irho - vtb * irho;
         gsc[c] = A1 - (R)0.5 * Sb * irho;
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(SP_NT) k_spectral_bwd(const R* __restrict__ X,
         const R B1 = gpc[c] + br[a][c];  // Gamma_P' (its own cotangent plus b's)
         const R Pb = rho * br[a][c] + rho * B1;
         const R ptb = mp ? Pb : (R)0;
-        drho += (double)br[a][c] * pp + (double)B1 * (pp - x) + (double)ptb * gp[c] * irho * irho;
+        drho_r += (double)(br[a][c] * pp + B1 * (pp - x) + ptb * gp[c] * irho * irho);
         out[c] = xs[a][c] + ptb - rho * B1;
         gpc[c] = B1 - ptb * irho;
       }
@@ -357,8 +359,8 @@ __global__ void __launch_bounds__(SP_NT) k_spectral_bwd(const R* __restrict__ X,
 #pragma unroll
   for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
   q[Q_XMIN] = 1e300;
-  q[1] = dmunu;
-  q[2] = drho;
+  q[1] = dmunu_r;
+  q[2] = drho_r;
   block_reduce_write<SP_NT>(q, partials + (size_t)blockIdx.x * MF_NQ);
 }
 

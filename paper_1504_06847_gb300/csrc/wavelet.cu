@@ -1001,17 +1001,24 @@ __global__ void __launch_bounds__(WNT) k_wav_ll(const R* __restrict__ in_img, si
 // coefficient arrays, one thread per output, and the adjoint of the
 // threshold / dual step.  Taps come from the constant tables with a runtime K.
 // ---------------------------------------------------------------------------
-template <class R>
-__global__ void k_ana_rows(const R* __restrict__ src, int sp, size_t ss, R* __restrict__ tmp, int M, int K,
-                           int nimg) {
+// Half-lengths of the bases of one launch (basis k = blockIdx.y).
+struct KList {
+  int K[MF_MAX_BASES];
+};
+
+// Row analysis of one level of one basis: tmp row r = [a_0..a_{M/2-1}, d_0..].
+template <class R, int K>
+__device__ __forceinline__ void ana_rows_k(const R* __restrict__ src, int sp, size_t ss, R* __restrict__ tmp, int M,
+                                           int nimg) {
+  constexpr int F = 2 * K;
   const size_t total = (size_t)nimg * M * (M / 2);
-  const int F = 2 * K;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % (M / 2));
     const int r = (int)((e / (M / 2)) % M);
     const size_t img = e / ((size_t)M * (M / 2));
     const R* row = src + img * ss + (size_t)r * sp;
     R a = 0, d = 0;
+#pragma unroll
     for (int n = 0; n < F; n++) {
       const R v = row[(2 * i + n) & (M - 1)];
       a = fma(Taps<R>::h(K, n), v, a);
@@ -1023,17 +1030,19 @@ __global__ void k_ana_rows(const R* __restrict__ src, int sp, size_t ss, R* __re
   }
 }
 
-template <class R>
-__global__ void k_ana_cols(const R* __restrict__ tmp, int M, int K, int nimg, R* __restrict__ dst, int dp,
-                           size_t ds) {
+// Column analysis of tmp into the level's M x M block of dst (pitch dp).
+template <class R, int K>
+__device__ __forceinline__ void ana_cols_k(const R* __restrict__ tmp, int M, int nimg, R* __restrict__ dst, int dp,
+                                           size_t ds) {
+  constexpr int F = 2 * K;
   const size_t total = (size_t)nimg * (M / 2) * M;
-  const int F = 2 * K;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int c = (int)(e % M);
     const int i = (int)((e / M) % (M / 2));
     const size_t img = e / ((size_t)M * (M / 2));
     const R* t = tmp + img * (size_t)M * M + c;
     R a = 0, d = 0;
+#pragma unroll
     for (int n = 0; n < F; n++) {
       const R v = t[(size_t)((2 * i + n) & (M - 1)) * M];
       a = fma(Taps<R>::h(K, n), v, a);
@@ -1045,9 +1054,10 @@ __global__ void k_ana_cols(const R* __restrict__ tmp, int M, int K, int nimg, R*
   }
 }
 
-template <class R>
-__global__ void k_syn_cols(const R* __restrict__ src, int sp, size_t ss, R* __restrict__ tmp, int M, int K,
-                           int nimg) {
+// Column synthesis of the level's M x M block of src (pitch sp) into tmp.
+template <class R, int K>
+__device__ __forceinline__ void syn_cols_k(const R* __restrict__ src, int sp, size_t ss, R* __restrict__ tmp, int M,
+                                           int nimg) {
   const size_t total = (size_t)nimg * M * M;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int c = (int)(e % M);
@@ -1055,7 +1065,9 @@ __global__ void k_syn_cols(const R* __restrict__ src, int sp, size_t ss, R* __re
     const size_t img = e / ((size_t)M * M);
     const R* col = src + img * ss + c;
     R v = 0;
-    for (int n = (m & 1); n < 2 * K; n += 2) {
+#pragma unroll
+    for (int n2 = 0; n2 < K; n2++) {
+      const int n = 2 * n2 + (m & 1);
       const int i = ((m - n) >> 1) & (M / 2 - 1);
       v = fma(Taps<R>::h(K, n), col[(size_t)i * sp], v);
       v = fma(Taps<R>::g(K, n), col[(size_t)(M / 2 + i) * sp], v);
@@ -1064,23 +1076,73 @@ __global__ void k_syn_cols(const R* __restrict__ src, int sp, size_t ss, R* __re
   }
 }
 
+// Row synthesis of output (m, x) of one basis's tmp.
+template <class R, int K>
+__device__ __forceinline__ R syn_row_point(const R* __restrict__ row, int M, int x) {
+  R v = 0;
+#pragma unroll
+  for (int n2 = 0; n2 < K; n2++) {
+    const int n = 2 * n2 + (x & 1);
+    const int i = ((x - n) >> 1) & (M / 2 - 1);
+    v = fma(Taps<R>::h(K, n), row[i], v);
+    v = fma(Taps<R>::g(K, n), row[M / 2 + i], v);
+  }
+  return v;
+}
+
 template <class R>
-__global__ void k_syn_rows(const R* __restrict__ tmp, int M, int K, int nimg, R* __restrict__ dst, int dp,
-                           size_t ds, int accumulate) {
+__global__ void k_ana_rows(const R* __restrict__ src, size_t src_bs, int sp, size_t ss, R* __restrict__ tmp,
+                           size_t tmp_bs, int M, int nimg, KList ks) {
+  const int k = blockIdx.y;
+  MF_K_SWITCH(ks.K[k], (ana_rows_k<R, KK>(src + k * src_bs, sp, ss, tmp + k * tmp_bs, M, nimg)));
+}
+
+template <class R>
+__global__ void k_ana_cols(const R* __restrict__ tmp, size_t tmp_bs, int M, int nimg, R* __restrict__ dst,
+                           size_t dst_bs, int dp, size_t ds, KList ks) {
+  const int k = blockIdx.y;
+  MF_K_SWITCH(ks.K[k], (ana_cols_k<R, KK>(tmp + k * tmp_bs, M, nimg, dst + k * dst_bs, dp, ds)));
+}
+
+template <class R>
+__global__ void k_syn_cols(const R* __restrict__ src, size_t src_bs, int sp, size_t ss, R* __restrict__ tmp,
+                           size_t tmp_bs, int M, int nimg, KList ks) {
+  const int k = blockIdx.y;
+  MF_K_SWITCH(ks.K[k], (syn_cols_k<R, KK>(src + k * src_bs, sp, ss, tmp + k * tmp_bs, M, nimg)));
+}
+
+// Row synthesis into the level's block of each basis's coefficient array (j > 1).
+template <class R>
+__global__ void k_syn_rows(const R* __restrict__ tmp, size_t tmp_bs, int M, int nimg, R* __restrict__ dst,
+                           size_t dst_bs, int dp, size_t ds, KList ks) {
+  const int k = blockIdx.y;
   const size_t total = (size_t)nimg * M * M;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int x = (int)(e % M);
     const int m = (int)((e / M) % M);
     const size_t img = e / ((size_t)M * M);
-    const R* row = tmp + img * (size_t)M * M + (size_t)m * M;
+    const R* row = tmp + k * tmp_bs + img * (size_t)M * M + (size_t)m * M;
     R v = 0;
-    for (int n = (x & 1); n < 2 * K; n += 2) {
-      const int i = ((x - n) >> 1) & (M / 2 - 1);
-      v = fma(Taps<R>::h(K, n), row[i], v);
-      v = fma(Taps<R>::g(K, n), row[M / 2 + i], v);
+    MF_K_SWITCH(ks.K[k], (v = syn_row_point<R, KK>(row, M, x)));
+    dst[k * dst_bs + img * ds + (size_t)m * dp + x] = v;
+  }
+}
+
+// Level-1 row synthesis of every basis, summed and added into out (pitch M).
+template <class R>
+__global__ void k_syn_rows_sum(const R* __restrict__ tmp, size_t tmp_bs, int nd, int M, int nimg,
+                               R* __restrict__ out, KList ks) {
+  const size_t total = (size_t)nimg * M * M;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(e % M);
+    const int m = (int)((e / M) % M);
+    const size_t img = e / ((size_t)M * M);
+    R v = 0;
+    for (int k = 0; k < nd; k++) {
+      const R* row = tmp + k * tmp_bs + img * (size_t)M * M + (size_t)m * M;
+      MF_K_SWITCH(ks.K[k], (v += syn_row_point<R, KK>(row, M, x)));
     }
-    R* o = dst + img * ds + (size_t)m * dp + x;
-    *o = accumulate ? *o + v : v;
+    out[e] += v;
   }
 }
 
@@ -1095,13 +1157,17 @@ __global__ void k_wav_bwd_point(R* __restrict__ zc, const R* __restrict__ uc, co
                                 R* __restrict__ gc, size_t per_basis, int nd, const WavSet<R>* __restrict__ ws,
                                 R rho, R mu_s, double* __restrict__ partials) {
   const size_t total = per_basis * nd;
-  double dmu = 0.0, drho = 0.0;
-  const R tau = mu_s / rho;
+  // the forward's constants (formed in FP64, rounded once); each element's terms in
+  // the cube's precision, summed in FP64 (one add per element: FP64 multiplies and
+  // divisions per element are slow)
+  const R inv_rho = (R)(1.0 / (double)rho), tau = (R)((double)mu_s / (double)rho);
+  const R inv_rho2 = inv_rho * inv_rho;
+  double dmu_r = 0, drho_r = 0;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int k = (int)(e / per_basis);
     const R w = ws->w[k];
     const R z = zc[e], gam = gam_old[e], g1 = gc[e], ub = w * uc[e];
-    const R tt = z - gam / rho;
+    const R tt = z - gam * inv_rho;
     const bool m = fabs(tt) > tau;
     const R sg = tt > 0 ? (R)1 : (tt < 0 ? (R)-1 : (R)0);
     const R t = m ? tt - tau * sg : (R)0;
@@ -1109,11 +1175,11 @@ __global__ void k_wav_bwd_point(R* __restrict__ zc, const R* __restrict__ uc, co
     const R ttb = m ? tb : (R)0;
     const R taub = m ? -sg * tb : (R)0;
     zc[e] = -rho * g1 - rho * ub + ttb;
-    gc[e] = g1 + ub - ttb / rho;
-    dmu += (double)taub / rho;
-    drho += (double)g1 * (t - z) + (double)ub * (2 * t - z) - (double)taub * mu_s / (rho * rho) +
-            (double)ttb * gam / (rho * rho);
+    gc[e] = g1 + ub - ttb * inv_rho;
+    dmu_r += (double)taub;
+    drho_r += (double)(g1 * (t - z) + ub * (2 * t - z) + (ttb * gam - taub * mu_s) * inv_rho2);
   }
+  const double dmu = dmu_r * (double)inv_rho, drho = drho_r;
   double q[Q_COUNT];
 #pragma unroll
   for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
@@ -1128,18 +1194,20 @@ static unsigned simple_grid(size_t total) {
   return (unsigned)(b < 152 * 32 ? (b ? b : 1) : 152 * 32);
 }
 
+// Reverse-mode transforms over full coefficient arrays; every basis of a level
+// in one launch (grid y = basis), so tmp holds nd cubes (basis stride L N^2).
 template <class R>
 cudaError_t launch_wav_analysis_full(const R* src, R* coef, R* tmp, int N, int L, int J, int nd,
                                      const int* Ks, cudaStream_t s) {
-  const size_t NN = (size_t)N * N;
-  for (int k = 0; k < nd; k++) {
-    R* ck = coef + (size_t)k * L * NN;
-    for (int j = 1; j <= J; j++) {
-      const int M = N >> (j - 1);
-      const R* in = j == 1 ? src : ck;
-      k_ana_rows<R><<<simple_grid((size_t)L * M * (M / 2)), WNT, 0, s>>>(in, N, NN, tmp, M, Ks[k], L);
-      k_ana_cols<R><<<simple_grid((size_t)L * M * (M / 2)), WNT, 0, s>>>(tmp, M, Ks[k], L, ck, N, NN);
-    }
+  const size_t NN = (size_t)N * N, cube = (size_t)L * NN;
+  KList ks{};
+  for (int k = 0; k < nd; k++) ks.K[k] = Ks[k];
+  for (int j = 1; j <= J; j++) {
+    const int M = N >> (j - 1);
+    const dim3 g(simple_grid((size_t)L * M * (M / 2)), nd);
+    if (j == 1) k_ana_rows<R><<<g, WNT, 0, s>>>(src, 0, N, NN, tmp, cube, M, L, ks);
+    else k_ana_rows<R><<<g, WNT, 0, s>>>(coef, cube, N, NN, tmp, cube, M, L, ks);
+    k_ana_cols<R><<<g, WNT, 0, s>>>(tmp, cube, M, L, coef, cube, N, NN, ks);
   }
   return cudaGetLastError();
 }
@@ -1147,15 +1215,15 @@ cudaError_t launch_wav_analysis_full(const R* src, R* coef, R* tmp, int N, int L
 template <class R>
 cudaError_t launch_wav_synthesis_acc(R* coef, R* out, R* tmp, int N, int L, int J, int nd, const int* Ks,
                                      cudaStream_t s) {
-  const size_t NN = (size_t)N * N;
-  for (int k = 0; k < nd; k++) {
-    R* ck = coef + (size_t)k * L * NN;
-    for (int j = J; j >= 1; j--) {
-      const int M = N >> (j - 1);
-      k_syn_cols<R><<<simple_grid((size_t)L * M * M), WNT, 0, s>>>(ck, N, NN, tmp, M, Ks[k], L);
-      if (j == 1) k_syn_rows<R><<<simple_grid((size_t)L * M * M), WNT, 0, s>>>(tmp, M, Ks[k], L, out, N, NN, 1);
-      else k_syn_rows<R><<<simple_grid((size_t)L * M * M), WNT, 0, s>>>(tmp, M, Ks[k], L, ck, N, NN, 0);
-    }
+  const size_t NN = (size_t)N * N, cube = (size_t)L * NN;
+  KList ks{};
+  for (int k = 0; k < nd; k++) ks.K[k] = Ks[k];
+  for (int j = J; j >= 1; j--) {
+    const int M = N >> (j - 1);
+    const dim3 g(simple_grid((size_t)L * M * M), nd);
+    k_syn_cols<R><<<g, WNT, 0, s>>>(coef, cube, N, NN, tmp, cube, M, L, ks);
+    if (j == 1) k_syn_rows_sum<R><<<simple_grid((size_t)L * M * M), WNT, 0, s>>>(tmp, cube, nd, M, L, out, ks);
+    else k_syn_rows<R><<<g, WNT, 0, s>>>(tmp, cube, M, L, coef, cube, N, NN, ks);
   }
   return cudaGetLastError();
 }

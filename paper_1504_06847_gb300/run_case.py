@@ -2,9 +2,12 @@
 
   python -m paper_1504_06847_gb300.run_case --N 1024 --L 8 --iters 2 [--precision fp32|splitbf16]
       [--tile 64|32] [--J 3] [--resid]
+  python -m paper_1504_06847_gb300.run_case --batch 16 --iters 100      # batched form, timed
+  python -m paper_1504_06847_gb300.run_case --N 256 --L 32 --iters 20 --backward   # differentiable form, timed
 
-Prints the plan's report.  The cube follows the synthetic recipe of
-paper_1504_06847_gb300.synth (seeded sources, disk-array PSF, 20 dB noise).
+Prints the plan's report (or, for --batch / --backward, the measured times as
+JSON).  The cubes follow the synthetic recipe of paper_1504_06847_gb300.synth
+(seeded sources, disk-array PSF, 20 dB noise).
 """
 
 from __future__ import annotations
@@ -27,7 +30,13 @@ def main(argv=None):
     ap.add_argument("--tile", type=int, default=64, choices=[64, 32])
     ap.add_argument("--resid", action="store_true")
     ap.add_argument("--seed", type=int, default=9)
+    ap.add_argument("--batch", type=int, default=0, help="time the batched form on this many uneven cubes")
+    ap.add_argument("--backward", action="store_true", help="time forward and reverse pass of --iters iterations")
     a = ap.parse_args(argv)
+    if a.batch:
+        return run_batch(a)
+    if a.backward:
+        return run_backward(a)
     c = synth.make_cube(a.N, a.L, n_sources=max(2, int(40 * (a.N / 256) ** 2)), n_antennas=128, seed=a.seed)
     plan = Plan(torch.tensor(c.psf, dtype=torch.float32, device="cuda"))
     plan.set_option(MF_OPT_WAV_TILE, a.tile)
@@ -35,6 +44,70 @@ def main(argv=None):
     plan.iterate(torch.tensor(c.y, dtype=torch.float32, device="cuda"), a.iters, wavelet_levels=a.J,
                  precision=prec, resid_every=1 if a.resid else 0, **synth.WORKLOAD_PARAMS)
     print(json.dumps(plan.report()))
+
+
+def _events():
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_batch(a):
+    """Batched form: every cube's iterations in one graph launch, against the
+    same cubes iterated one plan after the other."""
+    from . import batch_iterate
+
+    cubes = synth.batch_workload(a.batch)
+    plans = [Plan(torch.tensor(c.psf, dtype=torch.float32, device="cuda")) for c in cubes]
+    ys = [torch.tensor(c.y, dtype=torch.float32, device="cuda") for c in cubes]
+    prm = synth.WORKLOAD_PARAMS
+    vox = sum(c.y.size for c in cubes)
+    batch_iterate(plans, ys, 2, **prm)
+    s, e = _events()
+    s.record()
+    batch_iterate(plans, ys, a.iters, **prm)
+    e.record()
+    torch.cuda.synchronize()
+    t_batch = s.elapsed_time(e)
+    for p, y in zip(plans, ys):
+        p.iterate(y, 2, **prm)
+    s.record()
+    for p, y in zip(plans, ys):
+        p.iterate(y, a.iters, **prm)
+    e.record()
+    torch.cuda.synchronize()
+    t_solo = s.elapsed_time(e)
+    print(json.dumps({"form": "batched", "cubes": a.batch, "shapes": synth.batch_shapes(a.batch), "iters": a.iters,
+                      "voxels": vox, "batch_ms": t_batch, "batch_voxel_it_per_s": vox * a.iters / (t_batch * 1e-3),
+                      "sequential_ms": t_solo, "sequential_voxel_it_per_s": vox * a.iters / (t_solo * 1e-3)}))
+
+
+def run_backward(a):
+    """Differentiable form: forward of --iters iterations from the zero state and
+    the reverse pass (tied rho) for L = ||X_K - X_true||^2."""
+    c = synth.make_cube(a.N, a.L, n_sources=max(2, int(40 * (a.N / 256) ** 2)), n_antennas=256, seed=a.seed)
+    plan = Plan(torch.tensor(c.psf, dtype=torch.float32, device="cuda"))
+    y = torch.tensor(c.y, dtype=torch.float32, device="cuda")
+    truth = torch.tensor(c.sky, dtype=torch.float32, device="cuda")
+    prm = synth.WORKLOAD_PARAMS
+    kw = dict(mu_eps=prm["mu_eps"], mu_s=prm["mu_s"], mu_nu=prm["mu_nu"])
+    plan.iterate(y, a.iters, rho_P=1.0, rho_T=1.0, rho_V=1.0, rho_S=1.0, **kw)
+    g = 2 * (plan.x() - truth)
+    plan.backward(y, a.iters, g, rho=1.0, **kw)
+    s, e = _events()
+    s.record()
+    plan.iterate(y, a.iters, rho_P=1.0, rho_T=1.0, rho_V=1.0, rho_S=1.0, **kw)
+    e.record()
+    torch.cuda.synchronize()
+    t_fwd = s.elapsed_time(e)
+    s.record()
+    _, dms, dmn, dr = plan.backward(y, a.iters, g, rho=1.0, **kw)
+    e.record()
+    torch.cuda.synchronize()
+    t_bwd = s.elapsed_time(e)
+    vox = c.y.size
+    print(json.dumps({"form": "differentiable", "N": a.N, "L": a.L, "iters": a.iters, "forward_ms": t_fwd,
+                      "backward_ms": t_bwd, "backward_over_forward": t_bwd / t_fwd,
+                      "forward_voxel_it_per_s": vox * a.iters / (t_fwd * 1e-3),
+                      "dL_dmu_s": dms, "dL_dmu_nu": dmn, "dL_drho": dr}))
 
 
 if __name__ == "__main__":

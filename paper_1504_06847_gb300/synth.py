@@ -129,3 +129,17 @@ PAPER_PARAMS = dict(mu_eps=0.001, mu_s=0.5, mu_nu=1.0,
 
 def workload(name: str) -> Cube:
     return make_cube(**WORKLOADS[name])
+
+
+def batch_shapes(count: int = 16, seed: int = 400):
+    """Uneven (N, L) shapes of the batched form: N in {128, 256, 512}, L in {16, 32, 64}."""
+    rng = np.random.default_rng(seed)
+    return [(int(rng.choice([128, 256, 512])), int(rng.choice([16, 32, 64]))) for _ in range(count)]
+
+
+def batch_workload(count: int = 16, seed: int = 400, n_antennas: int = 256):
+    """The cubes of the batched form: cube i has shape batch_shapes()[i], seed seed + i
+    and 40 (N/256)^2 sources."""
+    return [make_cube(N, L, n_sources=max(2, int(40 * (N / 256) ** 2)), n_antennas=n_antennas, seed=seed + i)
+            for i, (N, L) in enumerate(batch_shapes(count, seed))]
+
