@@ -4,6 +4,7 @@
       [--tile 64|32] [--J 3] [--resid]
   python -m paper_1504_06847_gb300.run_case --batch 16 --iters 100      # batched form, timed
   python -m paper_1504_06847_gb300.run_case --N 256 --L 32 --iters 20 --backward   # differentiable form, timed
+  python -m paper_1504_06847_gb300.run_case --N 1024 --L 64 --xstep    # step I: ours vs cuFFT (reference point)
 
 Prints the plan's report (or, for --batch / --backward, the measured times as
 JSON).  The cubes follow the synthetic recipe of paper_1504_06847_gb300.synth
@@ -32,7 +33,10 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=9)
     ap.add_argument("--batch", type=int, default=0, help="time the batched form on this many uneven cubes")
     ap.add_argument("--backward", action="store_true", help="time forward and reverse pass of --iters iterations")
+    ap.add_argument("--xstep", action="store_true", help="time step I against a cuFFT (torch.fft) reference point")
     a = ap.parse_args(argv)
+    if a.xstep:
+        return run_xstep(a)
     if a.batch:
         return run_batch(a)
     if a.backward:
@@ -108,6 +112,47 @@ def run_backward(a):
                       "backward_ms": t_bwd, "backward_over_forward": t_bwd / t_fwd,
                       "forward_voxel_it_per_s": vox * a.iters / (t_fwd * 1e-3),
                       "dL_dmu_s": dms, "dL_dmu_nu": dmn, "dL_drho": dr}))
+
+
+def run_xstep(a):
+    """Step I (X = c + g F(b), inverse FFT) of this library's kernels, against the
+    same filter applied with cuFFT through torch.fft (a reference point only: it
+    is not on this library's path)."""
+    c = synth.make_cube(a.N, a.L, n_sources=max(2, int(40 * (a.N / 256) ** 2)), n_antennas=128, seed=a.seed)
+    prm = synth.WORKLOAD_PARAMS
+    psf = torch.tensor(c.psf, dtype=torch.float32, device="cuda")
+    y = torch.tensor(c.y, dtype=torch.float32, device="cuda")
+    plan = Plan(psf)
+    plan.iterate(y, 3, **prm)
+    plan.set_timing(True)
+    plan.iterate(y, 10, warm_start=1, **prm)
+    t = plan.timing()
+    plan.set_timing(False)
+    ours = sum(t[k][0] / max(t[k][1], 1) for k in ("rows_fwd", "cols_solve", "rows_inv"))
+    # reference: rfft2 / filter / irfft2 on the same shapes (FP32 complex)
+    rho_bar = prm["mu_eps"] + prm["rho_P"] + prm["rho_S"] + 9 * prm["rho_T"]
+    hh = torch.fft.rfft2(torch.fft.ifftshift(psf, dim=(-2, -1)))
+    g = 1.0 / (hh.abs() ** 2 + rho_bar)
+    cc = torch.conj(hh) * torch.fft.rfft2(y) * g
+    b = torch.randn_like(y)
+    xs = torch.empty_like(y)
+
+    def ref():
+        xs.copy_(torch.fft.irfft2(cc + g * torch.fft.rfft2(b), s=(a.N, a.N)))
+
+    for _ in range(3):
+        ref()
+    s, e = _events()
+    s.record()
+    for _ in range(10):
+        ref()
+    e.record()
+    torch.cuda.synchronize()
+    cufft = s.elapsed_time(e) / 10
+    vox = c.y.size
+    print(json.dumps({"form": "step I", "N": a.N, "L": a.L, "ours_ms": ours, "cufft_torch_ms": cufft,
+                      "ours_voxels_per_s": vox / (ours * 1e-3), "cufft_voxels_per_s": vox / (cufft * 1e-3),
+                      "kernels": {k: t[k][0] / max(t[k][1], 1) for k in ("rows_fwd", "cols_solve", "rows_inv")}}))
 
 
 if __name__ == "__main__":
