@@ -492,23 +492,29 @@ __device__ __forceinline__ void level_tile_t(const R* in, int off, R* rpair, R* 
   __syncthreads();
   after_rows();  // the input tile is free from here on
   // 2. column analysis of column c of both row-analysis outputs into coefficient
-  //    rows RB j..RB j+RB-1 of the four sub-bands, fused with 3. threshold and
+  //    rows RB2 j..RB2 j+RB2-1 of the four sub-bands, fused with 3. threshold and
   //    dual update of those coefficients.  The item issues its global loads (old
   //    Gamma_T, or the coarse reconstruction that replaces the low-low band below
   //    the coarsest level) before its FMAs.  Offsets are 32-bit within the band.
   {
+    // rows per item: chosen per filter length so that the items fill whole
+    // rounds of the CTA's threads (CW * ceil(CW / RB2) close to a multiple of WNT)
+    constexpr int RB2 = K == 1 ? 4 : K <= 4 ? 5 : K == 5 ? 6 : 3;
+    constexpr int NRUN2 = (CW + RB2 - 1) / RB2, NV2 = 2 * RB2 - 2 + F;
+    static_assert(RB2 * NRUN2 <= C::SR, "rows written");
+    static_assert(2 * RB2 * (NRUN2 - 1) + NV2 <= C::CR, "rows read");
     const int Mh = M / 2;
     const int ci0 = y0 / 2 - (K - 1), cj0 = x0 / 2 - (K - 1);
     const int MhN = Mh * N;
-    for (int it = tid; it < CW * NRUN; it += WNT) {
+    for (int it = tid; it < CW * NRUN2; it += WNT) {
       const int c = it % CW, j = it / CW;
       const int gc = (cj0 + c) & (Mh - 1);
       const bool own_c = (unsigned)(c - (K - 1)) < (unsigned)(T / 2);
-      R gtl[RB], gtr[RB], gbl[RB], gbr[RB];
-      int go[RB];
+      R gtl[RB2], gtr[RB2], gbl[RB2], gbr[RB2];
+      int go[RB2];
 #pragma unroll
-      for (int i = 0; i < RB; i++) {
-        const int row = RB * j + i;
+      for (int i = 0; i < RB2; i++) {
+        const int row = RB2 * j + i;
         const int gi = (ci0 + row) & (Mh - 1);
         go[i] = gi * N + gc;
         gtl[i] = gtr[i] = gbl[i] = gbr[i] = (R)0;
@@ -519,10 +525,10 @@ __device__ __forceinline__ void level_tile_t(const R* in, int off, R* rpair, R* 
           gbr[i] = gto[go[i] + MhN + Mh];
         }
       }
-      const P* col = rp + 2 * RB * j * B_CP + c;
-      P v[NV];
+      const P* col = rp + 2 * RB2 * j * B_CP + c;
+      P v[NV2];
 #pragma unroll
-      for (int t = 0; t < NV; t++) v[t] = col[t * B_CP];
+      for (int t = 0; t < NV2; t++) v[t] = col[t * B_CP];
       // residual terms of the item's owned coefficients, in the cube's precision,
       // folded into the FP64 sums once per item
       R r_dg = 0, r_l1 = 0;
@@ -542,14 +548,14 @@ __device__ __forceinline__ void level_tile_t(const R* in, int off, R* rpair, R* 
         return gn + sc.rho_T * tp;
       };
 #pragma unroll
-      for (int i = 0; i < RB; i++) {
+      for (int i = 0; i < RB2; i++) {
         P lo = mk2((R)0, (R)0), hi = mk2((R)0, (R)0);
 #pragma unroll
         for (int n = 0; n < F; n++) {
           lo = fma2(Taps2<R>::hh(K, n), v[2 * i + n], lo);
           hi = fma2(Taps2<R>::gg(K, n), v[2 * i + n], hi);
         }
-        const int row = RB * j + i;
+        const int row = RB2 * j + i;
         const bool own = own_c && (unsigned)(row - (K - 1)) < (unsigned)(T / 2);
         const R tl = rco != nullptr ? gtl[i] : update(lo.x, gtl[i], own, go[i]);
         top[row * B_CP + c] = mk2(tl, update(lo.y, gtr[i], own, go[i] + Mh));
