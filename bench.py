@@ -42,8 +42,8 @@ FALLBACK_HBM_GBS = 6800.0
 STEP_ALG_BYTES_PER_VOXEL = 146.0
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each kernel at the
 # benchmark workload (None where no capture of the current kernel exists).  Level 1:
-# captured at 1024 x 1024 x 8 (543.4 MB per launch) and scaled by the 8x bands.
-NCU_TRAFFIC_PER_LAUNCH = {"wav_level1": 8 * 543.4e6}
+# captured at 1024 x 1024 x 8 (541.3 MB per launch) and scaled by the 8x bands.
+NCU_TRAFFIC_PER_LAUNCH = {"wav_level1": 8 * 541.3e6}
 
 
 def _env_int(k, d):
