@@ -387,11 +387,12 @@ __global__ void __launch_bounds__(COLS_NT, 2) k_cols(cx<R>* __restrict__ work, c
       base[(size_t)ky * n + c] = cconj<R>(buf[e]);
     }
     if (MODE == 2) {
-      double q[Q_COUNT];
+      // in the cube's precision: FP32 plans take the FP32 warp stage of the reduction
+      R q[Q_COUNT];
 #pragma unroll
-      for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
-      q[Q_XMIN] = 1e300;
-      q[Q_FIT] = 0.5 * (double)fit / ((double)N * (double)N);
+      for (int i = 0; i < Q_COUNT; i++) q[i] = 0;
+      q[Q_XMIN] = (R)1e300;  // infinite in FP32; the reduction writes the FP64 sentinel
+      q[Q_FIT] = fit * (R)(0.5 / ((double)N * (double)N));
       block_reduce_write<COLS_NT>(q, partials + (size_t)blockIdx.x * MF_NQ);
     }
   }

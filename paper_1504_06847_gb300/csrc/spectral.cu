@@ -187,16 +187,17 @@ __global__ void __launch_bounds__(SP_NT) k_spectral(const R* __restrict__ X, R* 
     }
   }
   if (RESID) {
-    double q[Q_COUNT];
+    // in the cube's precision: FP32 plans take the FP32 warp stage of the reduction
+    R q[Q_COUNT];
 #pragma unroll
-    for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
-    q[Q_DGV] = (double)r_dgv;
-    q[Q_DGS] = (double)r_dgs;
-    q[Q_L1NU] = (double)r_l1;
-    q[Q_DGP] = (double)r_dgp;
-    q[Q_X2] = (double)r_x2;
-    q[Q_XMIN] = r_xmin < (R)3.0e38 ? (double)r_xmin : 1e300;
-    q[Q_NONFIN] = r_bad ? 1.0 : 0.0;
+    for (int i = 0; i < Q_COUNT; i++) q[i] = 0;
+    q[Q_DGV] = r_dgv;
+    q[Q_DGS] = r_dgs;
+    q[Q_L1NU] = r_l1;
+    q[Q_DGP] = r_dgp;
+    q[Q_X2] = r_x2;
+    q[Q_XMIN] = r_xmin < (R)3.0e38 ? r_xmin : (R)1e300;
+    q[Q_NONFIN] = r_bad ? (R)1 : (R)0;
     block_reduce_write<SP_NT>(q, partials + (size_t)blockIdx.x * MF_NQ);
   }
 }

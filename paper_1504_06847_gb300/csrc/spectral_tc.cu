@@ -329,16 +329,16 @@ __global__ void __launch_bounds__(TcCfg<LP>::NT, 2) k_spectral_tc(const float* _
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
   if (RESID) {
-    double q[Q_COUNT];
+    float q[Q_COUNT];
 #pragma unroll
-    for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
+    for (int i = 0; i < Q_COUNT; i++) q[i] = 0.f;
     q[Q_DGV] = r_dgv;
     q[Q_DGS] = r_dgs;
     q[Q_L1NU] = r_l1;
     q[Q_DGP] = r_dgp;
     q[Q_X2] = r_x2;
-    q[Q_XMIN] = r_xmin < 3.0e38f ? (double)r_xmin : 1e300;
-    q[Q_NONFIN] = r_bad ? 1.0 : 0.0;
+    q[Q_XMIN] = r_xmin;  // 3e38 (no voxel) becomes the FP64 sentinel in the reduction
+    q[Q_NONFIN] = r_bad ? 1.f : 0.f;
     block_reduce_write<NT>(q, partials + (size_t)blockIdx.x * MF_NQ);
   }
 }

@@ -727,7 +727,12 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_level1_t(const R* __re
     R* dst = b + band * NN + (size_t)(y0 + m) * N + x0 + x;
     *dst += bacc[m * C::BP + x];
   }
-  if (RESID) block_reduce_write<WNT>(q, partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * MF_NQ);
+  if (RESID) {
+    R qr[Q_COUNT];  // FP32 plans take the FP32 warp stage of the reduction
+#pragma unroll
+    for (int i = 0; i < Q_COUNT; i++) qr[i] = (R)q[i];
+    block_reduce_write<WNT>(qr, partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * MF_NQ);
+  }
 }
 
 // One basis of a coarser level on a T x T tile (its input tile already in
@@ -810,9 +815,13 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_levelj_t(const R* __re
                                                          more ? ws->K[k + 1] : 0)));
     __syncthreads();
   }
-  if (RESID)
+  if (RESID) {
+    R qr[Q_COUNT];  // FP32 plans take the FP32 warp stage of the reduction
+#pragma unroll
+    for (int i = 0; i < Q_COUNT; i++) qr[i] = (R)q[i];
     block_reduce_write<WNT>(
-        q, partials + (((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * MF_NQ);
+        qr, partials + (((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * MF_NQ);
+  }
 }
 
 // Low-low analysis: LL_j (M/2 x M/2) of the M x M input, for one basis per CTA
