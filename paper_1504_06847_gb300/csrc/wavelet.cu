@@ -366,13 +366,15 @@ struct TC {
   static_assert((IR * IP) % 2 == 0, "input tile size must keep the pair planes aligned");
 };
 
+// Shared memory of the T x T level kernels: the input tile, then the pair
+// plane of the row analysis / column synthesis (CR x CP pairs), then the two
+// sub-band pair planes (SR x CP pairs each); level 1 adds its accumulator.
 template <class R, int T>
-__device__ __forceinline__ R* tile_smem(R*& ra, R*& rd, R*& sb) {
+__device__ __forceinline__ R* tile_smem(R*& ra, R*& sb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* in = reinterpret_cast<R*>(smem_raw);
   ra = in + TC<T>::IR * TC<T>::IP;
-  rd = ra + TC<T>::CR * TC<T>::CP;
-  sb = rd + TC<T>::CR * TC<T>::CP;
+  sb = ra + 2 * TC<T>::CR * TC<T>::CP;
   return in;
 }
 
@@ -666,7 +668,7 @@ __device__ __forceinline__ void load_tile_t(const R* __restrict__ img, int M, in
 // operands instead of having all lengths' taps hoisted into registers across
 // the loop over bases.
 template <class R, int T, int K, int RESID>
-__device__ __noinline__ void level1_basis(const R* in, R* ra, R* rd, R* sb, R* bacc, int N, int y0, int x0,
+__device__ __noinline__ void level1_basis(const R* in, R* ra, R* sb, R* bacc, int N, int y0, int x0,
                                           const R* __restrict__ gto, R* __restrict__ gtn, const R* __restrict__ rco,
                                           IterScalars<R> sc, R w, double* q) {
   auto emit = [&](int, int m, int x, const R* v) {
@@ -686,8 +688,8 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_level1_t(const R* __re
                                                                   IterScalars<R> sc,
                                                                   double* __restrict__ partials) {
   typedef TC<T> C;
-  R *ra, *rd, *sb;
-  R* in = tile_smem<R, T>(ra, rd, sb);
+  R *ra, *sb;
+  R* in = tile_smem<R, T>(ra, sb);
   const int tpd = N / T;
   const int band = blockIdx.y;
   const int y0 = (blockIdx.x / tpd) * T, x0 = (blockIdx.x % tpd) * T;
@@ -718,7 +720,7 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_level1_t(const R* __re
       prefetch_level<R, T>(ws->K[k + 1], gto + g1,
                            coarsest ? nullptr : rco + ((size_t)(k + 1) * L + band) * (NN / 4), N, N, y0, x0);
     }
-    MF_K_SWITCH(ws->K[k], (level1_basis<R, T, KK, RESID>(in, ra, rd, sb, bacc, N, y0, x0, gto + gofs, gtn + gofs,
+    MF_K_SWITCH(ws->K[k], (level1_basis<R, T, KK, RESID>(in, ra, sb, bacc, N, y0, x0, gto + gofs, gtn + gofs,
                                                          rc, sc, w, q)));
     __syncthreads();
   }
@@ -779,8 +781,8 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_levelj_t(const R* __re
                                                                   int coarsest, const WavSet<R>* __restrict__ ws,
                                                                   IterScalars<R> sc,
                                                                   double* __restrict__ partials) {
-  R *ra, *rd, *sb;
-  R* in = tile_smem<R, T>(ra, rd, sb);
+  R *ra, *sb;
+  R* in = tile_smem<R, T>(ra, sb);
   const int tpd = M / T;
   const int band = blockIdx.y;
   const int y0 = (blockIdx.x / tpd) * T, x0 = (blockIdx.x % tpd) * T;
