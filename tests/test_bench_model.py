@@ -34,3 +34,24 @@ def test_single_level_dictionary_moves_no_coarse_bands():
     V = 256 * 256 * 8
     assert b["wav_ll"] == 0 and b["wav_levelj"] == 0
     assert b["wav_level1"] / V == pytest.approx(4 + 8 + 2 * 8 * 4)
+
+
+def test_clock_samples_summary(tmp_path):
+    # nvidia-smi --format=csv,noheader,nounits lines: index, sm, max sm, power, active mask,
+    # hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap
+    path = tmp_path / "clocks.csv"
+    path.write_text("0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+                    "0, 1995, 2070, 1350.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n"
+                    "0, 2040, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+                    "garbage line\n")
+    c = bench.ClockSampler(0)
+    c.path = str(path)
+    s = c.summary()
+    assert s["sm_mhz"] == 2040 and s["sm_max_mhz"] == 2070 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    assert not path.exists()  # the sample file is removed
+
+
+def test_clock_samples_missing():
+    c = bench.ClockSampler(0)
+    assert c.summary() is None
