@@ -7,10 +7,23 @@ synthetic cube, through the C ABI.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+Besides the contract's fields the line carries the batched form (16 uneven
+cubes, 100 iterations each, one graph launch), the differentiable form
+(20 unrolled iterations at 256 x 256 x 32, forward and reverse pass), step I
+against a cuFFT reference point, and the FP64 oracle on the host cores
+(3 iterations of the full workload, a 1-thread run, the paper's settings at
+256 x 256 x 15).
+
 Multi-GPU runs (torchrun, one rank per GPU) solve one independent replica of
 the cube per rank (the path has no exchange between cubes): weak scaling.
 The reference arm (--impl reference) times the FP64 CPU oracle on the host
-cores instead, on a 256 x 256 x 64 sample of the same workload recipe.
+cores instead, one Algorithm-1 iteration of the workload per step.
+
+Single cases for profiling (no JSON contract line):
+  python bench.py --case plain --N 1024 --L 8 --iters 2 [--precision fp32|splitbf16] [--tile 64|32] [--resid]
+  python bench.py --case batch [--batch 16] [--iters 100]
+  python bench.py --case backward --N 256 --L 32 --iters 20
+  python bench.py --case xstep --N 1024 --L 64
 """
 
 from __future__ import annotations
@@ -144,27 +157,62 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def cpu_baseline(seconds=15.0):
-    """The FP64 oracle as it stands, on every host core this process may use."""
+PAPER_SAMPLE = dict(N=256, L=15, n_sources=40, n_antennas=256, seed=15)
+PAPER_SAMPLE_NAME = "256x256x15 cube from the same recipe (seed 15, 40 sources, 256 antennas), the paper's Section 4 settings"
+ORACLE_SAMPLES = {"256x256x64": (SAMPLE, "WORKLOAD_PARAMS"), "256x256x15-paper": (PAPER_SAMPLE, "PAPER_PARAMS")}
+
+
+def _oracle_rate(pb, n_iter):
+    """voxel-it/s of n_iter oracle iterations after one untimed one, and the seconds taken."""
+    st = pb.zero_state()
+    pb.iterate(st, 1)
+    t0 = time.perf_counter()
+    pb.iterate(st, n_iter)
+    el = time.perf_counter() - t0
+    return pb.N * pb.N * pb.L * n_iter / el, el
+
+
+def oracle_case(name, n_iter):
+    """The oracle on one of the small samples (the 1-thread leg runs this in a child process)."""
+    import oracle
+    from paper_1504_06847_gb300 import synth
+
+    kw, params = ORACLE_SAMPLES[name]
+    c = synth.make_cube(**kw)
+    v, el = _oracle_rate(oracle.Problem(c.psf, c.y, getattr(synth, params)), n_iter)
+    return {"value": v, "seconds": el, "iters": n_iter}
+
+
+def cpu_baseline(cube):
+    """The FP64 oracle as it stands on the host cores: the benchmarked workload
+    itself over 3 iterations (the line's value), the 256 x 256 x 64 sample of
+    the same recipe on every core and on one, and the paper's own settings at
+    256 x 256 x 15 (the shape class of its Section 4 timing)."""
     cores = len(os.sched_getaffinity(0))
     os.environ["OMP_NUM_THREADS"] = str(cores)
     import oracle
     from paper_1504_06847_gb300 import synth
 
-    c = synth.make_cube(**SAMPLE)
-    pb = oracle.Problem(c.psf, c.y, synth.WORKLOAD_PARAMS)
-    st = pb.zero_state()
-    pb.iterate(st, 1)  # warm-up
-    n, t0 = 0, time.perf_counter()
-    while True:
-        pb.iterate(st, 1)
-        n += 1
-        el = time.perf_counter() - t0
-        if el >= seconds or n >= 200:
-            break
-    V = SAMPLE["N"] ** 2 * SAMPLE["L"]
-    return {"value": V * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} FP64 Algorithm-1 iterations of the {SAMPLE_NAME} ({el:.1f} s)"}
+    V = cube.y.size
+    full, full_s = _oracle_rate(oracle.Problem(cube.psf, cube.y, synth.WORKLOAD_PARAMS), 3)
+    sample = oracle_case("256x256x64", 20)
+    paper = oracle_case("256x256x15-paper", 40)
+    one = None
+    try:
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--case", "oracle", "--sample",
+                              "256x256x64", "--iters", "2"], env=env, capture_output=True, text=True, timeout=300)
+        one = json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:  # reported, not fatal
+        one = {"error": str(e)[:200]}
+    return {"value": full, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"3 FP64 Algorithm-1 iterations of the {WORKLOAD} workload itself ({full_s:.1f} s, "
+                      f"after one untimed iteration); value = {V} voxels x 3 / time",
+            "sample_256x256x64": {"value": sample["value"], "cores": cores, "iters": sample["iters"],
+                                  "note": SAMPLE_NAME},
+            "one_thread_256x256x64": dict(one, cores=1, note=SAMPLE_NAME),
+            "paper_settings_256x256x15": {"value": paper["value"], "cores": cores, "iters": paper["iters"],
+                                          "note": PAPER_SAMPLE_NAME}}
 
 
 def max_over_ranks(seconds, dist=None, device="cpu"):
@@ -184,6 +232,10 @@ def whole_job_rate(units_per_rank, seconds, world):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, one Algorithm-1
+    iteration per step of the benchmarked workload itself when the run stays
+    within a few minutes (K + W <= 40 steps of ~4 s), else of the 256 x 256 x 64
+    sample of the same recipe."""
     rank = _env_int("RANK", 0)
     if rank != 0:
         return 0
@@ -192,7 +244,9 @@ def run_reference(args):
     import oracle
     from paper_1504_06847_gb300 import synth
 
-    c = synth.make_cube(**SAMPLE)
+    full = args.steps + args.warmup <= 40
+    c = synth.workload(WORKLOAD) if full else synth.make_cube(**SAMPLE)
+    name = f"the {WORKLOAD} workload" if full else f"the {SAMPLE_NAME}"
     pb = oracle.Problem(c.psf, c.y, synth.WORKLOAD_PARAMS)
     st = pb.zero_state()
     for _ in range(args.warmup):
@@ -201,16 +255,167 @@ def run_reference(args):
     for _ in range(args.steps):
         pb.iterate(st, 1)
     el = time.perf_counter() - t0
-    V = SAMPLE["N"] ** 2 * SAMPLE["L"]
+    V = c.y.size
     value = V * args.steps / el
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": SAMPLE_NAME, "n_iter_per_step": 1},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": name, "n_iter_per_step": 1,
+                                            "same_config": full},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"one FP64 Algorithm-1 iteration of the {SAMPLE_NAME} per step"},
+                             "sample": f"one FP64 Algorithm-1 iteration of {name} per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def measure_forms(stream, xstep_ms=None):
+    """The batched and differentiable forms (and step I against cuFFT), timed
+    with CUDA events on `stream`."""
+    import torch
+
+    import paper_1504_06847_gb300 as mf
+    from paper_1504_06847_gb300 import synth
+
+    prm = synth.WORKLOAD_PARAMS
+    out = {}
+    with torch.cuda.stream(stream):
+        # batched form: 16 uneven cubes, 100 iterations each, one graph launch
+        cubes = synth.batch_workload(16)
+        plans = [mf.Plan(torch.tensor(c.psf, dtype=torch.float32, device="cuda")) for c in cubes]
+        ys = [torch.tensor(c.y, dtype=torch.float32, device="cuda") for c in cubes]
+        vox = sum(c.y.size for c in cubes)
+        n_it = 100
+        kw = dict(prm, stream=stream.cuda_stream)
+        mf.batch_iterate(plans, ys, 2, **kw)
+        s, e = _events(torch)
+        s.record(stream)
+        mf.batch_iterate(plans, ys, n_it, **kw)
+        e.record(stream)
+        stream.synchronize()
+        t_batch = s.elapsed_time(e)
+        s.record(stream)
+        for p_, y in zip(plans, ys):
+            p_.iterate(y, n_it, **kw)
+        e.record(stream)
+        stream.synchronize()
+        t_seq = s.elapsed_time(e)
+        out["batched"] = {"cubes": len(cubes), "shapes": synth.batch_shapes(16), "iters_each": n_it, "voxels": vox,
+                          "ms": t_batch, "voxel_it_per_s": vox * n_it / (t_batch * 1e-3),
+                          "sequential_ms": t_seq, "sequential_voxel_it_per_s": vox * n_it / (t_seq * 1e-3),
+                          "dtype": "f32"}
+        for p_ in plans:
+            p_.close()
+        del plans, ys
+        # differentiable form: 20 unrolled iterations at 256 x 256 x 32, forward + reverse
+        c = synth.workload("256x256x32")
+        K = 20
+        plan = mf.Plan(torch.tensor(c.psf, dtype=torch.float32, device="cuda"))
+        y = torch.tensor(c.y, dtype=torch.float32, device="cuda")
+        truth = torch.tensor(c.sky, dtype=torch.float32, device="cuda")
+        tied = dict(mu_eps=prm["mu_eps"], mu_s=prm["mu_s"], mu_nu=prm["mu_nu"])
+        rho = dict(rho_P=1.0, rho_T=1.0, rho_V=1.0, rho_S=1.0)
+        plan.iterate(y, K, stream=stream.cuda_stream, **tied, **rho)
+        g = 2 * (plan.x() - truth)
+        plan.backward(y, K, g, rho=1.0, stream=stream.cuda_stream, **tied)  # allocates the checkpoints
+        s.record(stream)
+        plan.iterate(y, K, stream=stream.cuda_stream, **tied, **rho)
+        e.record(stream)
+        stream.synchronize()
+        t_fwd = s.elapsed_time(e)
+        s.record(stream)
+        plan.backward(y, K, g, rho=1.0, stream=stream.cuda_stream, **tied)
+        e.record(stream)
+        stream.synchronize()
+        t_bwd = s.elapsed_time(e)
+        out["differentiable"] = {"N": 256, "L": 32, "unrolled_iters": K, "forward_ms": t_fwd,
+                                 "forward_and_reverse_ms": t_bwd,
+                                 "note": "the reverse pass re-runs the forward with per-iteration checkpoints",
+                                 "voxel_it_per_s_forward_and_reverse": c.y.size * K / (t_bwd * 1e-3),
+                                 "dtype": "f32"}
+        plan.close()
+    if xstep_ms is not None:
+        out["xstep_vs_cufft"] = xstep_reference(stream, xstep_ms)
+    return out
+
+
+def xstep_reference(stream, ours_ms):
+    """Step I of the benchmarked cube with cuFFT (torch.fft: rfft2, the filter,
+    irfft2), a reference point only: it is not on this library's path."""
+    import torch
+
+    from paper_1504_06847_gb300 import synth
+
+    c = synth.workload(WORKLOAD)
+    prm = synth.WORKLOAD_PARAMS
+    N = c.y.shape[-1]
+    with torch.cuda.stream(stream):
+        psf = torch.tensor(c.psf, dtype=torch.float32, device="cuda")
+        y = torch.tensor(c.y, dtype=torch.float32, device="cuda")
+        rho_bar = prm["mu_eps"] + prm["rho_P"] + prm["rho_S"] + 9 * prm["rho_T"]
+        hh = torch.fft.rfft2(torch.fft.ifftshift(psf, dim=(-2, -1)))
+        g = 1.0 / (hh.abs() ** 2 + rho_bar)
+        cc = torch.conj(hh) * torch.fft.rfft2(y) * g
+        b = torch.randn_like(y)
+        xs = torch.empty_like(y)
+
+        def ref():
+            xs.copy_(torch.fft.irfft2(cc + g * torch.fft.rfft2(b), s=(N, N)))
+
+        for _ in range(3):
+            ref()
+        s, e = _events(torch)
+        s.record(stream)
+        for _ in range(10):
+            ref()
+        e.record(stream)
+        stream.synchronize()
+    cufft = s.elapsed_time(e) / 10
+    return {"ours_ms": ours_ms, "cufft_torch_ms": cufft, "ours_over_cufft": ours_ms / cufft}
+
+
+def run_case(args):
+    """Single runs for profiling and quick checks (no contract line)."""
+    import torch
+
+    import paper_1504_06847_gb300 as mf
+    from paper_1504_06847_gb300 import synth
+
+    if args.case == "oracle":
+        print(json.dumps(oracle_case(args.sample, args.iters)))
+        return 0
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    if args.case == "batch":
+        print(json.dumps(measure_forms(stream)["batched"]))
+        return 0
+    if args.case == "backward":
+        print(json.dumps(measure_forms(stream)["differentiable"]))
+        return 0
+    c = synth.make_cube(args.N, args.L, n_sources=max(2, int(40 * (args.N / 256) ** 2)), n_antennas=128,
+                        seed=args.seed)
+    prm = synth.WORKLOAD_PARAMS
+    prec = mf.MF_FP32_DCT_SPLITBF16 if args.precision == "splitbf16" else mf.MF_FP32
+    with torch.cuda.stream(stream):
+        plan = mf.Plan(torch.tensor(c.psf, dtype=torch.float32, device="cuda"))
+        plan.set_option(mf.MF_OPT_WAV_TILE, args.tile)
+        y = torch.tensor(c.y, dtype=torch.float32, device="cuda")
+        if args.case == "xstep":
+            plan.iterate(y, 3, precision=prec, **prm)
+            plan.set_timing(True)
+            plan.iterate(y, 10, warm_start=1, precision=prec, **prm)
+            t = plan.timing()
+            plan.set_timing(False)
+            ours = sum(t[k][0] / max(t[k][1], 1) for k in ("rows_fwd", "cols_solve", "rows_inv"))
+            print(json.dumps(dict(xstep_reference(stream, ours), N=args.N, L=args.L)))
+            return 0
+        plan.iterate(y, args.iters, wavelet_levels=args.J, precision=prec, resid_every=1 if args.resid else 0,
+                     **prm)
+        print(json.dumps(plan.report()))
     return 0
 
 
@@ -221,9 +426,22 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="leave out the batched and differentiable forms")
     ap.add_argument("--precision", default="splitbf16", choices=["splitbf16", "fp32"],
                     help="DCT arithmetic of the spectral step (the cube is FP32 either way)")
+    ap.add_argument("--case", default=None, choices=["plain", "batch", "backward", "xstep", "oracle"],
+                    help="a single run for profiling instead of the benchmark line")
+    ap.add_argument("--N", type=int, default=1024)
+    ap.add_argument("--L", type=int, default=8)
+    ap.add_argument("--J", type=int, default=3)
+    ap.add_argument("--iters", type=int, default=2)
+    ap.add_argument("--tile", type=int, default=64, choices=[64, 32])
+    ap.add_argument("--resid", action="store_true")
+    ap.add_argument("--seed", type=int, default=9)
+    ap.add_argument("--sample", default="256x256x64", choices=sorted(ORACLE_SAMPLES))
     args = ap.parse_args()
+    if args.case is not None:
+        return run_case(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -281,22 +499,32 @@ def main():
     value = whole_job_rate(V * args.steps, ms * 1e-3, world)
     launches = sum(n for _, n in timing.values())
 
-    # --- end to end through the C ABI with host buffers: each step copies y from
-    # pinned host memory, runs one iteration with the FP64 residual report, reads it back ---
+    # --- end to end through the public API with host buffers: each step copies y
+    # from pinned host memory, runs one iteration with the FP64 residual report
+    # (primal and dual residuals, objective), reads the report and copies X back
+    # into pinned host memory ---
     y_host = torch.tensor(cube.y, dtype=torch.float32).pin_memory()
+    x_host = torch.empty(cube.y.shape, dtype=torch.float32).pin_memory()
     y_dev = torch.empty_like(y)
     params_e2e = plan.params(stream=stream.cuda_stream, warm_start=1, resid_every=1, precision=precision, **prm)
+    with torch.cuda.stream(stream):  # the dual residual's work cubes are allocated by the first such call
+        plan.iterate(y, 1, params_e2e)
+        plan.report()
     e2e_steps = max(3, min(args.steps, 10))
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         with torch.cuda.stream(stream):
             y_dev.copy_(y_host, non_blocking=True)
-        plan.iterate(y_dev, 1, params_e2e)
-        rep = plan.report()
+            plan.iterate(y_dev, 1, params_e2e)
+            rep = plan.report()
+            x_host.copy_(plan.x(), non_blocking=True)
+        stream.synchronize()
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e_value = whole_job_rate(V * e2e_steps, e2e_s, world)
+    if rep["status"] != mf.MF_OK:
+        raise RuntimeError(f"e2e report status {rep['status']}")
 
     if rank != 0:
         if dist is not None:
@@ -332,19 +560,23 @@ def main():
                    "dct": "split-BF16 tcgen05, FP32 accumulate" if args.precision == "splitbf16" else "FP32",
                    "n_iter_per_step": 1, "parallelism": "replicas" if world > 1 else "single",
                    "l2": f"inputs larger than L2 (plan working set {plan.device_bytes / 1e9:.1f} GB)",
-                   "params": prm},
+                   "resid_every": 0, "e2e_resid_every": 1, "params": prm},
         "roofline": roofline,
         "step_roofline": {"bound": "hbm", "alg_bytes_per_voxel": STEP_ALG_BYTES_PER_VOXEL, "achieved": step_ach,
                           "peak": peak, "unit": "GB/s", "frac": step_ach / peak},
         "kernels": per_kernel,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(y_host.numel() * 4),
-                "d2h_bytes_per_step": 16 * 8, "steps": e2e_steps,
-                "note": "per step: pinned y upload, one iteration with FP64 residuals, report read-back"},
+                "d2h_bytes_per_step": int(x_host.numel() * 4) + 16 * 8 + 4, "steps": e2e_steps,
+                "note": "per step: pinned y upload, one iteration with the FP64 primal/dual residuals and "
+                        "objective, report read-back, X copied back into pinned host memory"},
     }
     line["clocks"] = clk.summary()
+    if not args.no_forms:
+        xs = sum(per_kernel[k]["ms_per_launch"] for k in ("rows_fwd", "cols_solve", "rows_inv"))
+        line["forms"] = measure_forms(stream, xs)
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(cube)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

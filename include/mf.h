@@ -70,11 +70,16 @@ typedef struct {
 } mf_params;
 
 /* Filled by mf_plan_get_report, FP64 sums over the cube, measured after the
- * dual update of the last residual iteration:
+ * dual update of the last residual iteration (the residuals of the stopping
+ * rule Section 3 takes from Boyd et al. 2011, Sec. 3.3, for the two-block
+ * split (X, V) | (P, T, S) of Algorithm 1; d = change over that iteration):
  *   primal_res = ||P-X||^2 + ||T-W_s X||^2 + ||V-S W_nu||^2 + ||S-X||^2
- *              = sum_c ||dGamma_c||^2 / rho_c^2 (Boyd et al. 2011, Sec. 3.3);
+ *              = sum_c ||dGamma_c||^2 / rho_c^2;
+ *   dual_res   = ||rho_P dP + rho_T W_s^T dT + rho_S dS||^2 + rho_V^2 ||dS W_nu||^2;
  *   objective  = 1/2||Y-HX||^2 + mu_eps/2||X||^2 + mu_s||W_s X||_1 + mu_nu||X W_nu||_1;
- *   x_min      = min(X) (X may carry small negatives; P is its projection). */
+ *   x_min      = min(X) (X may carry small negatives; P is its projection).
+ * A plan's first call with resid_every > 0 allocates 5 more cubes for the
+ * dual residual's snapshots and work arrays (kept until the plan is destroyed). */
 typedef struct {
   int iters_done;
   int resid_iter;      /* iteration index the residual fields refer to (-1: none) */
@@ -83,6 +88,7 @@ typedef struct {
   double objective;
   double x_min;
   double x_norm2;
+  double dual_res;
 } mf_report;
 
 /* Defaults: mu_eps 0.001, mu_s 0.05, mu_nu 0.01, all rho 1, J 3, mask 0x1FF,
@@ -175,7 +181,8 @@ typedef enum {
   MF_K_WAV_LEVELJ = 6, /* step III: coarser fused levels */
   MF_K_SETUP = 7,      /* per-call constants: F(y), g, c; zeroing of the state */
   MF_K_REDUCE = 8,     /* FP64 fold of the residual partials */
-  MF_K_COUNT = 9
+  MF_K_DUAL = 9,       /* dual residual: snapshot before step I, reduction after the iteration */
+  MF_K_COUNT = 10
 } mf_kernel;
 
 /* Per-kernel CUDA-event timing of the plan's launches on its stream (off by
@@ -187,14 +194,29 @@ mf_status mf_plan_set_timing(mf_plan* p, int enable);
 mf_status mf_plan_get_timing(mf_plan* p, int kernel, double* total_ms, long long* launches);
 const char* mf_kernel_name(int kernel);
 
-/* Performance options of a plan.  They change launch shapes only: every option
- * value computes the same arithmetic per element in the same order, so
- * results are bitwise identical.
+/* Options of a plan (each call synchronises the plan's last stream).
  *   MF_OPT_WAV_TILE: output tile edge of the fused wavelet level kernels,
  *                    64 (default) or 32; levels smaller than the tile use
- *                    the largest tile that fits. */
-typedef enum { MF_OPT_WAV_TILE = 0 } mf_option;
+ *                    the largest tile that fits.  Launch shape only: every
+ *                    value computes the same arithmetic per element in the
+ *                    same order, so results are bitwise identical.
+ *   MF_OPT_TEST_TC_STALL: for tests of the failure path only.  A value v > 0
+ *                    makes CTA 0 of every later split-BF16 spectral launch
+ *                    skip its tensor-core product and its commit and give
+ *                    up on the completion wait after v SM cycles, with
+ *                    nothing in flight: the kernel records the expiry in the
+ *                    plan's device error word, frees its tensor memory and
+ *                    returns, and mf_plan_get_report returns MF_ERR_TIMEOUT.
+ *                    0 (default) turns it off. */
+typedef enum { MF_OPT_WAV_TILE = 0, MF_OPT_TEST_TC_STALL = 1 } mf_option;
 mf_status mf_plan_set_option(mf_plan* p, int option, int value);
+
+/* Synchronises the plan's last stream and clears its latched status and device
+ * error word, so that a plan whose bounded device wait expired (or whose
+ * reduction saw a non-finite value) accepts work again.  The state arrays may
+ * be inconsistent after such a failure: restart from the zero state
+ * (warm_start = 0) or restore a saved state. */
+mf_status mf_plan_clear_status(mf_plan* p);
 
 /* Host copy of the library's low-pass filter DbK (K = 1..8, 2K taps, double),
  * built at load time from Daubechies' spectral factorisation. */
@@ -210,27 +232,30 @@ const char* mf_status_string(mf_status s);
  *
  * The paper has no counterpart: this entry point exists for callers that may
  * not allocate device memory at all -- code running where cudaMalloc is
- * unavailable or forbidden (inside a host callback or another library's
- * allocator hook, under a caller-owned memory pool or budget, or a real-time
- * path that must not block on the allocator).  Plans need cudaMalloc; this
- * call does not.  Its working memory is one file-scope static __device__
+ * unavailable or forbidden (inside another library's allocator hook, under a
+ * caller-owned memory pool or budget, or a real-time path that must not block
+ * on the allocator).  Plans need cudaMalloc; this call does not.  Its working memory is one file-scope static __device__
  * array of about 10.4 MB (MF_XSTEP_NOALLOC_MAX_VOXELS = 2^19 voxels:
  * e.g. 256 x 256 x 8 or 128 x 128 x 32), which every GPU that loads the
  * library holds until the process exits.  Larger cubes return
  * MF_ERR_TOO_LARGE before any device work.
  *
  *   psf_cube, y_cube, b_cube : device [L][N][N] float inputs (read only)
- *   x_out                    : device [L][N][N] float output (also used as a
- *                              temporary during the call)
+ *   x_out                    : device [L][N][N] float output, written by the
+ *                              last kernel only, so it may alias psf_cube,
+ *                              y_cube or b_cube (an in-place solve)
  *   prm                      : mu_eps, rho_P, rho_T, rho_S, wavelet_mask and
  *                              stream are read; other fields are ignored.
- * The first call on a device looks up the static array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one array, which keeps
- * the last call's contents (each call overwrites everything it reads), so
- * calls whose work overlaps on the GPU -- on different streams or host
- * threads -- race; serialise them.  The work is enqueued on prm->stream and
- * the call returns; errors: MF_ERR_INVALID, MF_ERR_TOO_LARGE, MF_ERR_CUDA.
+ * All pointers belong to the current device.  The first call on a device
+ * looks up the static array's device address (cudaGetSymbolAddress) with
+ * that device current and keeps it; make that first call before any stream
+ * capture, and do not use this entry point on a device after a
+ * cudaDeviceReset of it (the kept address is then stale).  Every call shares
+ * the one array, which keeps the last call's contents (each call overwrites
+ * everything it reads), so calls whose work overlaps on the GPU -- on
+ * different streams or host threads -- race; serialise them.  The call copies
+ * nothing from the host: it enqueues kernels on prm->stream and returns;
+ * errors: MF_ERR_INVALID, MF_ERR_TOO_LARGE, MF_ERR_CUDA.
  */
 #define MF_XSTEP_NOALLOC_MAX_VOXELS (1u << 19)
 mf_status mf_xstep_noalloc(int N, int L, const float* psf_cube, const float* y_cube, const float* b_cube,

@@ -24,11 +24,11 @@ EXPORTS = ["mf_params_default", "mf_plan_create", "mf_plan_create_f64", "mf_plan
            "mf_plan_set_array", "mf_plan_get_state", "mf_plan_set_state", "mf_plan_get_report",
            "mf_wavelet_filter", "mf_status_string", "mf_plan_set_timing", "mf_plan_get_timing",
            "mf_kernel_name", "mf_xstep_noalloc", "mf_plan_set_option", "mf_batch_iterate",
-           "mf_admm_backward"]
-MF_OPT_WAV_TILE = 0
+           "mf_admm_backward", "mf_plan_clear_status"]
+MF_OPT_WAV_TILE, MF_OPT_TEST_TC_STALL = 0, 1
 
 KERNELS = ["rows_fwd", "cols_solve", "rows_inv", "spectral", "wav_ll", "wav_level1", "wav_levelj", "setup",
-           "reduce"]
+           "reduce", "dual"]
 
 
 class MFError(RuntimeError):
@@ -50,7 +50,7 @@ class Report(ctypes.Structure):
     _fields_ = [("iters_done", ctypes.c_int), ("resid_iter", ctypes.c_int),
                 ("primal_res", ctypes.c_double), ("dual_gamma", ctypes.c_double),
                 ("objective", ctypes.c_double), ("x_min", ctypes.c_double),
-                ("x_norm2", ctypes.c_double)]
+                ("x_norm2", ctypes.c_double), ("dual_res", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -111,6 +111,8 @@ def lib():
         L.mf_admm_backward.restype = ctypes.c_int
         L.mf_plan_set_option.argtypes = [vp, ctypes.c_int, ctypes.c_int]
         L.mf_plan_set_option.restype = ctypes.c_int
+        L.mf_plan_clear_status.argtypes = [vp]
+        L.mf_plan_clear_status.restype = ctypes.c_int
         L.mf_xstep_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.POINTER(Params), vp]
         L.mf_xstep_noalloc.restype = ctypes.c_int
         _lib = L
@@ -179,12 +181,16 @@ def xstep_noalloc(psf, y, b, x_out, **kw):
     for t in (psf, y, b, x_out):
         if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != (L_, N_, N_):
             raise ValueError("psf, y, b, x_out must be contiguous float32 CUDA tensors [L, N, N]")
-    if "stream" not in kw:
-        kw["stream"] = torch.cuda.current_stream(y.device).cuda_stream
-    p = default_params(**kw)
-    _check(lib().mf_xstep_noalloc(N_, L_, ctypes.c_void_p(psf.data_ptr()), ctypes.c_void_p(y.data_ptr()),
-                                  ctypes.c_void_p(b.data_ptr()), ctypes.byref(p), ctypes.c_void_p(x_out.data_ptr())),
-           "mf_xstep_noalloc")
+        if t.device != y.device:
+            raise ValueError("psf, y, b, x_out must be on one device")
+    # the library uses the static array and launches on the current device
+    with torch.cuda.device(y.device):
+        if "stream" not in kw:
+            kw["stream"] = torch.cuda.current_stream(y.device).cuda_stream
+        p = default_params(**kw)
+        _check(lib().mf_xstep_noalloc(N_, L_, ctypes.c_void_p(psf.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                      ctypes.c_void_p(b.data_ptr()), ctypes.byref(p),
+                                      ctypes.c_void_p(x_out.data_ptr())), "mf_xstep_noalloc")
 
 
 class Plan:
@@ -276,6 +282,10 @@ class Plan:
     def set_option(self, option: int, value: int):
         """Launch-shape option (results are bitwise identical for every value)."""
         _check(lib().mf_plan_set_option(self._h, option, value), "mf_plan_set_option")
+
+    def clear_status(self):
+        """Clears a latched failure status (see mf_plan_clear_status)."""
+        _check(lib().mf_plan_clear_status(self._h), "mf_plan_clear_status")
 
     def set_timing(self, enable: bool):
         """Per-kernel CUDA-event timing on the plan's stream (resets the counters)."""

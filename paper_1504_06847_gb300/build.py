@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmf.so")
-SOURCES = ["plan.cu", "fft.cu", "spectral.cu", "spectral_tc.cu", "wavelet.cu", "noalloc.cu", "backward.cu", "daub.cpp"]
+SOURCES = ["plan.cu", "fft.cu", "spectral.cu", "spectral_tc.cu", "wavelet.cu", "noalloc.cu", "backward.cu", "dual.cu",
+           "daub.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

@@ -16,6 +16,7 @@
 #define MF_MAX_LEVELS 8
 #define MF_MAX_L 128
 #define MF_NQ 16          // reduction quantities per block partial
+#define MF_AUX_GRID (152 * 8)  // largest grid of the grid-stride reduction kernels (dual residual)
 
 namespace mf {
 
@@ -57,6 +58,8 @@ enum {
   Q_FIT,       // 1/2 ||Y - H X||^2
   Q_XMIN,      // min X (reduced with min)
   Q_NONFIN,    // count of non-finite values met
+  Q_DUALX,     // ||rho_P dP + rho_T W_s^T dT + rho_S dS||^2 (dual residual, X part)
+  Q_DS2,       // ||d(S W_nu)||^2
   Q_COUNT
 };
 
@@ -98,6 +101,8 @@ struct mf_plan {
   void* wset;        // WavSet of the current call (device)
   void* dct_tc;      // split-BF16 DCT operands of the precision form (device), or null
   int* err;          // device error word (bounded waits that expired)
+  void* dual;        // dual-residual snapshots and work cubes (allocated on first use)
+  size_t dual_bytes;
   size_t total_bytes;
   cudaStream_t stream;
   mf_status status;
@@ -107,6 +112,7 @@ struct mf_plan {
   double rho_weights[4];
   mf_params last_params;
   int wav_tile;         // preferred wavelet tile edge (MF_OPT_WAV_TILE)
+  long long tc_stall;   // MF_OPT_TEST_TC_STALL (0: off)
   void* batch_exec;     // last batch graph launched with this plan first (cudaGraphExec_t)
   cudaStream_t batch_stream;
   // per-kernel timing
@@ -158,15 +164,16 @@ template <class R> cudaError_t launch_wav_level(const R* in, size_t in_band_stri
                                                 const R* rcoarse, R* out, const R* gt_old, R* gt_new,
                                                 int N, int M, int L, int coarsest, int nd, const WavSet<R>* ws,
                                                 IterScalars<R> sc, double* partials, int resid, int pref_tile,
-                                                cudaStream_t s);
+                                                int* err, cudaStream_t s);
 template <class R> int wav_level_blocks(int M, int L, int nd, int pref_tile);
 // Precision form of the spectral step: DCTs as split-BF16 tcgen05 products (L <= 64).
 int spectral_tc_lp_of(int L);                        // padded L (16, 32, 48, 64) or 0
 size_t spectral_tc_operand_elems(int L);             // BF16 elements of the DCT operands
 void spectral_tc_build_operands(int L, uint16_t* out);  // host: C and C^T split hi/lo, core layout
+// stall > 0: CTA 0 skips its product and waits at most stall cycles (test of the timeout path).
 cudaError_t launch_spectral_tc(const float* X, float* GP, float* Sd, float* GV, float* GSd, float* b,
                                const uint16_t* bmats, int N, int L, IterScalars<float> sc, double* partials,
-                               int resid, int* err, cudaStream_t s);
+                               int resid, int* err, long long stall, cudaStream_t s);
 int spectral_tc_blocks(int N);
 
 // Copies the Daubechies tap tables into the wavelet kernels' constant memory
@@ -177,5 +184,12 @@ cudaError_t upload_taps();
 template <class R> cudaError_t launch_shift_psf(const R* psf, R* out, int N, size_t total, cudaStream_t s);
 
 cudaError_t launch_finalize(const double* partials, int nblocks, double* sums, int accumulate, cudaStream_t s);
+
+// Dual residual of residual iterations (dual.cu): cubes of p->dual, the
+// snapshot taken before step I, and the reduction after the iteration.
+size_t dual_cubes();
+template <class R> cudaError_t dual_snapshot(mf_plan* p, cudaStream_t s);
+template <class R> cudaError_t dual_finish(mf_plan* p, const R* gt_old, const R* gt_new, int J, int nd,
+                                           const int* Ks, const R* w, cudaStream_t s);
 
 }  // namespace mf

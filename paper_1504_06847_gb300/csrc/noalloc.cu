@@ -31,7 +31,10 @@ constexpr int kMaxDevices = 64;
 float* g_scratch_ptr[kMaxDevices] = {nullptr};
 std::mutex g_scratch_mutex;
 
-// Device address of the static array on the current device (looked up once).
+// Device address of the static array on the current device, looked up by the
+// first call on that device (with the device current) and kept for later
+// calls.  A cudaDeviceReset of that device unloads the module and leaves the
+// kept address stale; mf.h states that the entry point is not for use after one.
 cudaError_t scratch_for_current_device(float** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -49,6 +52,17 @@ cudaError_t scratch_for_current_device(float** out) {
 }
 
 bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// tw[k] = exp(-2 pi i k / N): the angle's cosine and sine in FP64, rounded
+// once to FP32 (the plans build the same table on the host).
+__global__ void k_twiddles(cx<float>* tw, int N) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    double sn, cs;
+    sincospi(-2.0 * (double)k / (double)N, &sn, &cs);
+    tw[k].x = (float)cs;
+    tw[k].y = (float)sn;
+  }
+}
 
 }  // namespace
 
@@ -81,16 +95,14 @@ extern "C" mf_status mf_xstep_noalloc(int N, int L, const float* psf, const floa
   C* tw = reinterpret_cast<C*>(base + 4 * V + V / 2 + kMaxNyq);
 
   cudaStream_t s = (cudaStream_t)prm->stream;
-  C tw_host[kMaxN];
-  for (int k = 0; k < N; k++) {
-    const double ang = -2.0 * M_PI * (double)k / (double)N;
-    tw_host[k].x = (float)std::cos(ang);
-    tw_host[k].y = (float)std::sin(ang);
-  }
-  cudaError_t e = cudaMemcpyAsync(tw, tw_host, sizeof(C) * N, cudaMemcpyHostToDevice, s);
-  // transfer function: F(ifftshift(psf)), with x_out as the shifted-PSF temporary
-  if (!e) e = launch_shift_psf<float>(psf, x_out, N, V, s);
-  if (!e) e = launch_rows_fwd<float>(x_out, work, N, N * L, tw, s);
+  k_twiddles<<<(N + 255) / 256, 256, 0, s>>>(tw, N);
+  cudaError_t e = cudaGetLastError();
+  // transfer function: F(ifftshift(psf)); the shifted PSF (V floats) waits in
+  // the cc region, which is free until the constants are formed, so that x_out
+  // is written by the last pass only (x_out may alias psf, y or b)
+  float* shifted = reinterpret_cast<float*>(cc);
+  if (!e) e = launch_shift_psf<float>(psf, shifted, N, V, s);
+  if (!e) e = launch_rows_fwd<float>(shifted, work, N, N * L, tw, s);
   if (!e)
     e = launch_cols<float>(work, N, L, tw, 0, hhat, hhat_nyq, nullptr, nullptr, nullptr, nullptr, nullptr,
                            nullptr, nullptr, nullptr, nullptr, s);

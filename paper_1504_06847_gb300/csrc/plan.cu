@@ -93,11 +93,13 @@ struct Alloc {
 void free_plan_memory(mf_plan* p) {
   void* ptrs[] = {p->X, p->b, p->GP, p->Sd, p->GV, p->GSd, p->GT[0], p->GT[1], p->work, p->hhat, p->hhat_nyq,
                   p->yhat, p->yhat_nyq, p->cc, p->cc_nyq, p->gg, p->gg_nyq, p->tw, p->dctC, p->scratch,
-                  p->partials, p->sums, p->wset, p->dct_tc, p->err, p->bwd_buf};
+                  p->partials, p->sums, p->wset, p->dct_tc, p->err, p->bwd_buf, p->dual};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   p->bwd_buf = nullptr;
   p->bwd_bytes = 0;
+  p->dual = nullptr;
+  p->dual_bytes = 0;
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   p->ev_pool.clear();
 }
@@ -159,6 +161,7 @@ mf_status create(int N, int L, const R* psf, mf_plan** out) {
   }
   const size_t colblocks = (size_t)L * N;  // upper bound of the column kernel's grid
   if (colblocks > cap) cap = colblocks;
+  if ((size_t)MF_AUX_GRID > cap) cap = MF_AUX_GRID;
   p->partial_cap = cap;
   p->partials = (double*)a.get(cap * MF_NQ * sizeof(double));
   p->sums = (double*)a.get(MF_NQ * sizeof(double));
@@ -277,7 +280,7 @@ cudaError_t spectral_step<float>(mf_plan* p, const IterScalars<float>& sc, int r
   if (precision == MF_FP32_DCT_SPLITBF16)
     return launch_spectral_tc((const float*)p->X, (float*)p->GP, (float*)p->Sd, (float*)p->GV, (float*)p->GSd,
                               (float*)p->b, (const uint16_t*)p->dct_tc, p->N, p->L, sc, p->partials, resid, p->err,
-                              s);
+                              p->tc_stall, s);
   return launch_spectral<float>((const float*)p->X, (float*)p->GP, (float*)p->Sd, (float*)p->GV, (float*)p->GSd,
                                 (float*)p->b, (const float*)p->dctC, p->N, p->L, sc, p->partials, resid, s);
 }
@@ -288,11 +291,16 @@ int spectral_grid(const mf_plan* p, int precision) {
 }
 
 template <class R>
-cudaError_t iteration(mf_plan* p, int J, int nd, const WavSet<R>* wsd, const IterScalars<R>& sc, int resid,
-                      int precision, cudaStream_t s) {
-  const int N = p->N, L = p->L;
+cudaError_t iteration(mf_plan* p, int J, const WavSet<R>& ws, const WavSet<R>* wsd, const IterScalars<R>& sc,
+                      int resid, int precision, cudaStream_t s) {
+  const int N = p->N, L = p->L, nd = ws.nd;
   const size_t NN = (size_t)N * N;
   cudaError_t e;
+  if (resid) {
+    // state entering the iteration, for the dual residual
+    Timed t(p, MF_K_DUAL, s);
+    if ((e = dual_snapshot<R>(p, s))) return e;
+  }
   // step I
   {
     Timed t(p, MF_K_ROWS_FWD, s);
@@ -355,7 +363,7 @@ cudaError_t iteration(mf_plan* p, int J, int nd, const WavSet<R>* wsd, const Ite
     {
       Timed t(p, j == 1 ? MF_K_WAV_LEVEL1 : MF_K_WAV_LEVELJ, s);
       if ((e = launch_wav_level<R>(in, 0, 0, rco, outp, gto, gtn, N, M, L, j == J, nd, wsd, sc, p->partials,
-                                   resid, p->wav_tile, s)))
+                                   resid, p->wav_tile, p->err, s)))
         return e;
     }
     if (resid) {
@@ -363,6 +371,12 @@ cudaError_t iteration(mf_plan* p, int J, int nd, const WavSet<R>* wsd, const Ite
       if ((e = launch_finalize(p->partials, wav_level_blocks<R>(M, L, M == N ? 1 : nd, p->wav_tile), p->sums, 1, s)))
         return e;
     }
+  }
+  if (resid) {
+    Timed t(p, MF_K_DUAL, s);
+    int Ks[MF_MAX_BASES];
+    for (int k = 0; k < nd; k++) Ks[k] = ws.K[k];
+    if ((e = dual_finish<R>(p, gto, gtn, J, nd, Ks, ws.w, s))) return e;
   }
   p->gt_cur = 1 - p->gt_cur;
   return cudaSuccess;
@@ -395,6 +409,16 @@ mf_status prepare(mf_plan* p, const R* y, const mf_params* prm, int n_iter, cuda
   sc.inv_VS = (R)(1.0 / (prm->rho_V + prm->rho_S));
   if (prm->warm_start && p->nd_state != ws.nd && p->iters_done > 0)
     return MF_ERR_INVALID;  // the stored Gamma_T belongs to another dictionary
+  if (prm->resid_every > 0 && !p->dual) {
+    // snapshots and work cubes of the dual residual, kept by the plan from now on
+    const size_t bytes = dual_cubes() * p->cube * sizeof(R);
+    if (cudaMalloc(&p->dual, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p->dual = nullptr;
+      return MF_ERR_OOM;
+    }
+    p->dual_bytes = bytes;
+  }
   cudaError_t e = cudaMemcpyAsync(p->wset, &ws, sizeof(ws), cudaMemcpyHostToDevice, s);
   {
     // constants: F(y), g, c
@@ -434,7 +458,7 @@ cudaError_t run_iterations(mf_plan* p, const mf_params* prm, int n_iter, const W
   cudaError_t e = cudaSuccess;
   for (int it = 0; it < n_iter && !e; it++) {
     const int resid = prm->resid_every > 0 && (((it + 1) % prm->resid_every) == 0 || it == n_iter - 1);
-    e = iteration<R>(p, prm->wavelet_levels, ws.nd, (const WavSet<R>*)p->wset, sc, resid, prm->precision, s);
+    e = iteration<R>(p, prm->wavelet_levels, ws, (const WavSet<R>*)p->wset, sc, resid, prm->precision, s);
     if (!e && resid) {
       p->report_pending = 1;
       p->report.resid_iter = p->iters_done + it + 1;
@@ -584,7 +608,7 @@ mf_status mf_internal_prepare_f32(mf_plan* p, const float* y, const mf_params* p
 }
 cudaError_t mf_internal_iteration_f32(mf_plan* p, const mf_params* prm, const WavSet<float>& ws,
                                       const IterScalars<float>& sc, cudaStream_t s) {
-  return iteration<float>(p, prm->wavelet_levels, ws.nd, (const WavSet<float>*)p->wset, sc, 0, prm->precision, s);
+  return iteration<float>(p, prm->wavelet_levels, ws, (const WavSet<float>*)p->wset, sc, 0, prm->precision, s);
 }
 void mf_internal_finish(mf_plan* p, const mf_params* prm, int n_iter) { finish(p, prm, n_iter); }
 
@@ -617,7 +641,7 @@ void mf_plan_destroy(mf_plan* p) {
   delete p;
 }
 
-size_t mf_plan_device_bytes(const mf_plan* p) { return p ? p->total_bytes + p->bwd_bytes : 0; }
+size_t mf_plan_device_bytes(const mf_plan* p) { return p ? p->total_bytes + p->bwd_bytes + p->dual_bytes : 0; }
 
 mf_status mf_admm_iterate(mf_plan* p, const float* y, const mf_params* prm, int n_iter) {
   return iterate<float>(p, y, prm, n_iter);
@@ -717,6 +741,7 @@ mf_status mf_plan_get_report(mf_plan* p, mf_report* r) {
     p->report.primal_res = q[Q_DGP] / (w[0] * w[0]) + q[Q_DGT] / (w[1] * w[1]) + q[Q_DGV] / (w[2] * w[2]) +
                            q[Q_DGS] / (w[3] * w[3]);
     p->report.dual_gamma = q[Q_DGP] + q[Q_DGT] + q[Q_DGV] + q[Q_DGS];
+    p->report.dual_res = q[Q_DUALX] + w[2] * w[2] * q[Q_DS2];
     const mf_params* pr = &p->last_params;
     p->report.objective = q[Q_FIT] + 0.5 * pr->mu_eps * q[Q_X2] + pr->mu_s * q[Q_L1S] + pr->mu_nu * q[Q_L1NU];
     p->report.x_min = q[Q_XMIN];
@@ -760,13 +785,26 @@ mf_status mf_plan_set_option(mf_plan* p, int option, int value) {
       if (cudaStreamSynchronize(p->stream) != cudaSuccess) return MF_ERR_CUDA;
       p->wav_tile = value;
       return MF_OK;
+    case MF_OPT_TEST_TC_STALL:
+      if (value < 0) return MF_ERR_INVALID;
+      if (cudaStreamSynchronize(p->stream) != cudaSuccess) return MF_ERR_CUDA;
+      p->tc_stall = value;
+      return MF_OK;
     default: return MF_ERR_INVALID;
   }
 }
 
+mf_status mf_plan_clear_status(mf_plan* p) {
+  if (!p) return MF_ERR_INVALID;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return MF_ERR_CUDA;
+  if (cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess) return MF_ERR_CUDA;
+  p->status = MF_OK;
+  return MF_OK;
+}
+
 const char* mf_kernel_name(int kernel) {
   static const char* names[MF_K_COUNT] = {"rows_fwd", "cols_solve", "rows_inv", "spectral", "wav_ll",
-                                          "wav_level1", "wav_levelj", "setup", "reduce"};
+                                          "wav_level1", "wav_levelj", "setup", "reduce", "dual"};
   return (kernel >= 0 && kernel < MF_K_COUNT) ? names[kernel] : "unknown";
 }
 

@@ -5,6 +5,12 @@
 
 namespace mf {
 
+// The neutral value of the min slot in a kernel's per-thread sums (FP32
+// values >= 3e38 become the FP64 sentinel 1e300 in the reduction).
+template <class R> struct NoMin;
+template <> struct NoMin<float> { static constexpr float v = 3.0e38f; };
+template <> struct NoMin<double> { static constexpr double v = 1.0e300; };
+
 // Reduces the Q_COUNT per-thread values over the CTA in a fixed order and
 // writes one MF_NQ-wide row of partials (thread count NT, multiple of 32).
 template <int NT>

@@ -458,7 +458,7 @@ template int spectral_blocks<double>(int, int);
 
 // FP64 fold of the per-block partials into sums[MF_NQ]: a fixed thread count
 // and a fixed tree order, so the result does not depend on scheduling.
-constexpr int FIN_NT = 512;
+constexpr int FIN_NT = 256;
 __global__ void __launch_bounds__(FIN_NT) k_finalize(const double* __restrict__ partials, int nblocks,
                                                       double* __restrict__ sums, int accumulate) {
   __shared__ double red[Q_COUNT][FIN_NT];

@@ -79,11 +79,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait; false when the limit expired.
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+// Bounded wait; false when the limit (in SM clock cycles) expired.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
   while (!mbar_try_wait(mbar, parity)) {
-    if (clock64() - t0 > TC_WAIT_CYCLES) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
 }
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(TcCfg<LP>::NT, 2) k_spectral_tc(const float* _
                                                            float* __restrict__ GSd, float* __restrict__ b,
                                                            const uint16_t* __restrict__ bmats, int NN, int L,
                                                            IterScalars<float> sc, double* __restrict__ partials,
-                                                           int* __restrict__ err) {
+                                                           int* __restrict__ err, long long stall_cycles) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   uint16_t* B1hi = reinterpret_cast<uint16_t*>(smem_raw);  // C as (N = k) x (K = l)
   uint16_t* B1lo = B1hi + LP * LP;
@@ -232,12 +232,16 @@ __global__ void __launch_bounds__(TcCfg<LP>::NT, 2) k_spectral_tc(const float* _
   const uint32_t tmem = *tslot;
   const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
 
-  // x^ = X W_nu
-  if (tid == 0) {
+  // x^ = X W_nu.  With stall_cycles > 0 (a test of the timeout path) CTA 0
+  // issues neither the product nor its commit, so nothing is in flight when
+  // its wait of stall_cycles cycles runs out.
+  const bool stalled = stall_cycles > 0 && blockIdx.x == 0;
+  const long long limit = stalled ? stall_cycles : TC_WAIT_CYCLES;
+  if (tid == 0 && !stalled) {
     issue_split_gemm<LP>(tmem, Ahi, Alo, B1hi, B1lo);
     mma_commit(mbar);
   }
-  bool ok = mbar_wait(mbar, 0);
+  bool ok = mbar_wait(mbar, 0, limit);
   tc_fence_after();
 
   // residual terms of this thread's voxels in FP32, folded into the FP64
@@ -291,7 +295,7 @@ __global__ void __launch_bounds__(TcCfg<LP>::NT, 2) k_spectral_tc(const float* _
     issue_split_gemm<LP>(tmem, Ahi, Alo, B2hi, B2lo);
     mma_commit(mbar);
   }
-  if (ok) ok = mbar_wait(mbar, 1);
+  if (ok) ok = mbar_wait(mbar, 1, limit);
   tc_fence_after();
 
   if (ok) {
@@ -346,7 +350,7 @@ __global__ void __launch_bounds__(TcCfg<LP>::NT, 2) k_spectral_tc(const float* _
 template <int LP>
 cudaError_t spectral_tc_lp(const float* X, float* GP, float* Sd, float* GV, float* GSd, float* b,
                            const uint16_t* bmats, int N, int L, IterScalars<float> sc, double* partials, int resid,
-                           int* err, cudaStream_t s) {
+                           int* err, long long stall, cudaStream_t s) {
   const int NN = N * N;
   const size_t sm = 4 * LP * LP * 2 + 2 * TC_M * LP * 2 + LP * TC_M * 4 + 16;
   const int blocks = NN / TC_M;
@@ -354,11 +358,13 @@ cudaError_t spectral_tc_lp(const float* X, float* GP, float* Sd, float* GV, floa
   if (resid) {
     e = cudaFuncSetAttribute(k_spectral_tc<LP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_spectral_tc<LP, 1><<<blocks, TcCfg<LP>::NT, sm, s>>>(X, GP, Sd, GV, GSd, b, bmats, NN, L, sc, partials, err);
+    k_spectral_tc<LP, 1><<<blocks, TcCfg<LP>::NT, sm, s>>>(X, GP, Sd, GV, GSd, b, bmats, NN, L, sc, partials, err,
+                                                           stall);
   } else {
     e = cudaFuncSetAttribute(k_spectral_tc<LP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_spectral_tc<LP, 0><<<blocks, TcCfg<LP>::NT, sm, s>>>(X, GP, Sd, GV, GSd, b, bmats, NN, L, sc, partials, err);
+    k_spectral_tc<LP, 0><<<blocks, TcCfg<LP>::NT, sm, s>>>(X, GP, Sd, GV, GSd, b, bmats, NN, L, sc, partials, err,
+                                                           stall);
   }
   return cudaGetLastError();
 }
@@ -411,12 +417,12 @@ void spectral_tc_build_operands(int L, uint16_t* out) {
 
 cudaError_t launch_spectral_tc(const float* X, float* GP, float* Sd, float* GV, float* GSd, float* b,
                                const uint16_t* bmats, int N, int L, IterScalars<float> sc, double* partials,
-                               int resid, int* err, cudaStream_t s) {
+                               int resid, int* err, long long stall, cudaStream_t s) {
   switch (spectral_tc_lp_of(L)) {
-    case 16: return spectral_tc_lp<16>(X, GP, Sd, GV, GSd, b, bmats, N, L, sc, partials, resid, err, s);
-    case 32: return spectral_tc_lp<32>(X, GP, Sd, GV, GSd, b, bmats, N, L, sc, partials, resid, err, s);
-    case 48: return spectral_tc_lp<48>(X, GP, Sd, GV, GSd, b, bmats, N, L, sc, partials, resid, err, s);
-    case 64: return spectral_tc_lp<64>(X, GP, Sd, GV, GSd, b, bmats, N, L, sc, partials, resid, err, s);
+    case 16: return spectral_tc_lp<16>(X, GP, Sd, GV, GSd, b, bmats, N, L, sc, partials, resid, err, stall, s);
+    case 32: return spectral_tc_lp<32>(X, GP, Sd, GV, GSd, b, bmats, N, L, sc, partials, resid, err, stall, s);
+    case 48: return spectral_tc_lp<48>(X, GP, Sd, GV, GSd, b, bmats, N, L, sc, partials, resid, err, stall, s);
+    case 64: return spectral_tc_lp<64>(X, GP, Sd, GV, GSd, b, bmats, N, L, sc, partials, resid, err, stall, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1330,7 +1330,7 @@ static cudaError_t launch_level_t(const R* in, const R* rcoarse, R* out, const R
 template <class R>
 cudaError_t launch_wav_level(const R* in, size_t, size_t, const R* rcoarse, R* out, const R* gt_old, R* gt_new,
                              int N, int M, int L, int coarsest, int nd, const WavSet<R>* ws, IterScalars<R> sc,
-                             double* partials, int resid, int pref_tile, cudaStream_t s) {
+                             double* partials, int resid, int pref_tile, int*, cudaStream_t s) {
   const int T = level_tile_edge(M, pref_tile);
   if (T == 64)
     return launch_level_t<R, 64>(in, rcoarse, out, gt_old, gt_new, N, M, L, coarsest, nd, ws, sc, partials, resid, s);
@@ -1359,7 +1359,7 @@ cudaError_t launch_wav_level(const R* in, size_t, size_t, const R* rcoarse, R* o
   template cudaError_t launch_wav_ll<R>(const R*, size_t, size_t, R*, int, int, int, const WavSet<R>*,            \
                                         cudaStream_t);                                                          \
   template cudaError_t launch_wav_level<R>(const R*, size_t, size_t, const R*, R*, const R*, R*, int, int, int,   \
-                                           int, int, const WavSet<R>*, IterScalars<R>, double*, int, int,        \
+                                           int, int, const WavSet<R>*, IterScalars<R>, double*, int, int, int*,  \
                                            cudaStream_t);
 INST(float)
 INST(double)
@@ -1369,6 +1369,8 @@ template cudaError_t launch_wav_analysis_full<float>(const float*, float*, float
                                                      cudaStream_t);
 template cudaError_t launch_wav_synthesis_acc<float>(float*, float*, float*, int, int, int, int, const int*,
                                                      cudaStream_t);
+template cudaError_t launch_wav_synthesis_acc<double>(double*, double*, double*, int, int, int, int, const int*,
+                                                      cudaStream_t);
 template cudaError_t launch_wav_bwd_point<float>(float*, const float*, const float*, float*, size_t, int,
                                                  const WavSet<float>*, float, float, double*, int*, cudaStream_t);
 

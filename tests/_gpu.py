@@ -51,16 +51,18 @@ def oracle_view(pb, st):
 def scales(pb, st):
     """Error scale of each compared array.  X, S W_nu and b: their own max.
     A multiplier is updated by rho_c times a constraint residual (step VI), so
-    its FP32 rounding floor is set by rho_c times the primal operand it
-    compares: Gamma_P and Gamma_S by rho |X|, Gamma_V by rho_V |S W_nu|,
-    Gamma_T by rho_T |W_s X|."""
+    its rounding floor is set by rho_c times the primal operand of its
+    constraint, in the domain the multiplier is compared in: Gamma_P by
+    rho_P |X|; Gamma_S, compared as Gamma_S W_nu, by rho_S |X W_nu|; Gamma_V
+    (DCT domain) by rho_V |S W_nu|; Gamma_T by rho_T |W_s X|."""
     p = pb.params
     C = oracle.dct_matrix(pb.L)
     xm = np.abs(st["X"]).max()
+    xdm = np.abs(np.einsum("kl,lij->kij", C, st["X"])).max()
     sm = np.abs(np.einsum("kl,lij->kij", C, st["S"])).max()
     zm = max(np.abs(oracle.dwt2(st["X"], h, pb.J)).max() for _, h in pb.bases)
     bm = np.abs(pb.make_b(st) - pb.HtY).max()
-    return {"X": xm, "Sd": sm, "b": bm, "GP": p["rho_P"] * xm, "GSd": p["rho_S"] * xm,
+    return {"X": xm, "Sd": sm, "b": bm, "GP": p["rho_P"] * xm, "GSd": p["rho_S"] * xdm,
             "GV": p["rho_V"] * sm, "GT": p["rho_T"] * zm}
 
 

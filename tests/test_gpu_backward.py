@@ -75,25 +75,63 @@ def test_autograd_function_agrees_with_plan_backward():
     assert abs(rh.grad.item() - dr) <= 1e-9 * max(1.0, abs(dr))
 
 
-def test_scalar_gradients_match_oracle_finite_differences_256x256x32():
-    # the differentiable-form workload: 256 x 256 x 32, 20 unrolled iterations
+def _lockstep(c, prm_p, prm_m, K, J, y_p=None, y_m=None):
+    """Losses of the oracle's +h and -h runs, iterated side by side, and how
+    many positivity / threshold decisions (P, T, V nonzero) differ between
+    them over all K iterations, out of how many."""
+    a = oracle.Problem(c.psf, c.y if y_p is None else y_p, prm_p, J=J)
+    b = oracle.Problem(c.psf, c.y if y_m is None else y_m, prm_m, J=J)
+    sa, sb = a.zero_state(), b.zero_state()
+    flips = decisions = 0
+    for _ in range(K):
+        a.iterate(sa, 1)
+        b.iterate(sb, 1)
+        for key in ("P", "T", "V"):
+            flips += int(np.count_nonzero((sa[key] != 0) != (sb[key] != 0)))
+            decisions += sa[key].size
+    loss = lambda st: float(((st["X"] - c.sky) ** 2).sum())
+    return loss(sa), loss(sb), flips, decisions
+
+
+def _tied(mu_s, mu_nu, rho):
+    return dict(mu_eps=0.001, mu_s=mu_s, mu_nu=mu_nu, rho_P=rho, rho_T=rho, rho_V=rho, rho_S=rho)
+
+
+def test_gradients_match_oracle_finite_differences_256x256x32():
+    """The differentiable-form workload (256 x 256 x 32, K = 20) against central
+    differences of the FP64 oracle.  At this size the number of decisions that
+    flip between the +h and -h runs is proportional to h (about 1e-6 of them
+    per 1e-5 of step for mu_s), so no usable step avoids every kink: the test
+    bounds the flipped fraction and requires the quotients at h and h/10 to
+    agree within the tolerance (the kinks crossed do not move them), then
+    compares the CUDA gradients with the quotient at h.  dL/dy is checked
+    along a seeded random unit direction and along its own direction (which
+    checks its norm)."""
     c = synth.workload("256x256x32")
     K, J = 20, 3
     dy, dms, dmn, dr = _gpu_grads(c, K, J)
-
-    def loss(mu_s, mu_nu, rho):
-        prm = dict(mu_eps=0.001, mu_s=mu_s, mu_nu=mu_nu, rho_P=rho, rho_T=rho, rho_V=rho, rho_S=rho)
-        st, _ = oracle.Problem(c.psf, c.y, prm, J=J).run(K)
-        return float(((st["X"] - c.sky) ** 2).sum())
-
-    h = 1e-4
-    for i, (g, base) in enumerate(((dms, 0.05), (dmn, 0.01), (dr, 1.0))):
-        args_p = [0.05, 0.01, 1.0]
-        args_m = [0.05, 0.01, 1.0]
-        args_p[i] = base + h
-        args_m[i] = base - h
-        fd = (loss(*args_p) - loss(*args_m)) / (2 * h)
-        assert abs(g - fd) <= 1e-3 * max(abs(fd), 1.0), (i, g, fd)
+    base = [0.05, 0.01, 1.0]
+    h = 1e-5
+    for i, g in enumerate((dms, dmn, dr)):
+        fds = []
+        for step in (h, h / 10):
+            p_, m_ = list(base), list(base)
+            p_[i] += step
+            m_[i] -= step
+            lp, lm, flips, n = _lockstep(c, _tied(*p_), _tied(*m_), K, J)
+            assert flips <= 1e-4 * n, (i, step, flips, n)
+            fds.append((lp - lm) / (2 * step))
+        tol = 1e-3 * max(abs(fds[0]), 1.0)
+        assert abs(fds[0] - fds[1]) <= tol, (i, fds)
+        assert abs(g - fds[0]) <= tol, (i, g, fds)
+    rng = np.random.default_rng(23)
+    d_rand = rng.normal(size=dy.shape)
+    for d in (d_rand / np.linalg.norm(d_rand), dy / np.linalg.norm(dy)):
+        lp, lm, flips, n = _lockstep(c, _tied(*base), _tied(*base), K, J, y_p=c.y + h * d, y_m=c.y - h * d)
+        assert flips <= 1e-4 * n, flips
+        fd = (lp - lm) / (2 * h)
+        g = float(np.sum(dy * d))
+        assert abs(g - fd) <= 1e-3 * max(abs(fd), 1.0), (g, fd)
 
 
 def test_backward_rejects_untied_penalties():

@@ -124,7 +124,25 @@ def test_residual_report_matches_oracle():
     assert abs(rep["x_min"] - H[-1, 4]) < 1e-12
     assert abs(rep["x_norm2"] - H[-1, 5]) < 1e-10 * H[-1, 5]
     assert abs(rep["objective"] - H[-1, 3]) < 1e-9 * H[-1, 3], (rep, H[-1])
+    # Boyd dual residual of the (X, V) | (P, T, S) split
+    assert abs(rep["dual_res"] - H[-1, 1]) < 1e-9 * H[-1, 1], (rep["dual_res"], H[-1, 1])
     assert p["rho_P"] == 1.0
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-9), (torch.float32, 1e-3)])
+def test_dual_residual_distinct_penalties(dtype, tol):
+    # distinct rho_c, so a penalty applied to the wrong term shows; the first
+    # iterations, where every term of the change is large
+    prm = dict(mu_eps=0.003, mu_s=0.04, mu_nu=0.015, rho_P=0.7, rho_T=1.3, rho_V=1.9, rho_S=0.6)
+    c = synth.make_cube(32, 6, n_sources=3, n_antennas=24, seed=17)
+    pb = oracle.Problem(c.psf, c.y, prm, J=2)
+    _, H = pb.run(3, hist=True)
+    plan = _gpu.run_gpu(c, prm, 3, J=2, dtype=dtype, resid_every=1)
+    rep = plan.report()
+    assert rep["status"] == mf.MF_OK and rep["resid_iter"] == 3
+    err = abs(rep["dual_res"] - H[-1, 1]) / H[-1, 1]
+    _gpu.log_errors({"dual_res": err})
+    assert err < tol, err
 
 
 def test_deterministic():

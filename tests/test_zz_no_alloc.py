@@ -49,22 +49,39 @@ def _plan_step_one(cube, b):
 
 @pytest.mark.gpu
 def test_noalloc_xstep_matches_plan_path_on_two_calls():
+    """Consecutive calls with different shapes and PSFs (so the second cannot
+    reuse the first one's transfer function, Nyquist columns or twiddles left
+    in the static array), each against the plan path's step I; the smaller
+    case also against the oracle's step I (Eq. linsystemX, solved with the
+    Fourier filter of Section 3), and an in-place call (x_out aliasing b)."""
     import __graft_entry__
+    import oracle
 
     __graft_entry__.build()
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    cube = synth.make_cube(128, 16, n_sources=8, n_antennas=64, seed=11)  # 2^18 voxels
-    assert 128 * 128 * 16 <= mf.XSTEP_NOALLOC_MAX_VOXELS
     rng = np.random.default_rng(5)
-    psf = torch.tensor(cube.psf, dtype=torch.float32, device="cuda")
-    y = torch.tensor(cube.y, dtype=torch.float32, device="cuda")
-    x_out = torch.empty_like(y)
-    for call in range(2):
+    cases = [synth.make_cube(128, 16, n_sources=8, n_antennas=64, seed=11),   # 2^18 voxels
+             synth.make_cube(64, 8, n_sources=4, n_antennas=40, seed=12)]
+    for call, cube in enumerate(cases):
+        L, N = cube.y.shape[0], cube.y.shape[-1]
+        assert N * N * L <= mf.XSTEP_NOALLOC_MAX_VOXELS
+        psf = torch.tensor(cube.psf, dtype=torch.float32, device="cuda")
+        y = torch.tensor(cube.y, dtype=torch.float32, device="cuda")
         b = torch.tensor(0.3 * rng.normal(size=cube.y.shape), dtype=torch.float32, device="cuda")
         ref = _plan_step_one(cube, b)
-        x_out.fill_(float("nan"))
+        x_out = torch.full_like(y, float("nan"))
         mf.xstep_noalloc(psf, y, b, x_out, **PRM)
         torch.cuda.synchronize()
         err = (x_out - ref).abs().max().item() / ref.abs().max().item()
         assert err < 1e-6, (call, err)
+        if call == 1:
+            pb = oracle.Problem(cube.psf, cube.y, PRM)
+            xo = pb.solve(pb.HtY + b.double().cpu().numpy())
+            x = x_out.double().cpu().numpy()
+            assert np.abs(x - xo).max() / np.abs(xo).max() < 1e-5
+            # in place: the result replaces b
+            bb = b.clone()
+            mf.xstep_noalloc(psf, y, bb, bb, **PRM)
+            torch.cuda.synchronize()
+            assert torch.equal(bb, x_out)
