@@ -225,6 +225,25 @@ mf_status mf_wavelet_filter(int K, double* taps_host, int* len);
 const char* mf_status_string(mf_status s);
 
 /*
+ * Spectral-index map (the post-processing of the paper's first simulation,
+ * Section 4): every pixel spectrum of cube is fitted, in a log scale, by the
+ * second-order power law
+ *   log S(nu) = c + alpha log(nu/nu0) + beta log^2(nu/nu0)
+ * by least squares over the L >= 3 bands.
+ *   cube       : device [L][N][N] float (e.g. X after mf_admm_iterate)
+ *   nu         : host, L band frequencies (> 0, at least 3 distinct); nu0 > 0
+ *   floor      : a pixel with any S(nu_l) <= floor has no log-scale fit and
+ *                gets NaN in all three outputs
+ *   c0_out, alpha_out, beta_out : device [N][N] float outputs (any may be NULL,
+ *                not all)
+ *   stream     : cudaStream_t (NULL = legacy default); the call enqueues one
+ *                kernel and returns.
+ * Errors: MF_ERR_INVALID (sizes, frequencies), MF_ERR_CUDA.
+ */
+mf_status mf_spectral_index(int N, int L, const float* cube, const double* nu, double nu0, float floor,
+                            float* c0_out, float* alpha_out, float* beta_out, void* stream);
+
+/*
  * Step I without any allocation: x = (H^T H + rho I)^-1 (H^T y + b) per band,
  * rho = mu_eps + rho_S + rho_P + n_s rho_T with n_s the number of bases in
  * prm->wavelet_mask -- the same solve, on the same kernels, as the first step

@@ -196,3 +196,23 @@ class Problem:
                                    _p(st["V"]), _p(st["S"]), _p(st["GP"]), _p(st["GT"]),
                                    _p(st["GV"]), _p(st["GS"]))
         assert rc == 0
+
+
+# ---------------------------------------------------------------------------
+# Spectral-index fit (post-processing of the paper's first simulation, Section 4)
+# ---------------------------------------------------------------------------
+
+def spectral_index(cube: np.ndarray, nu, nu0: float | None = None, floor: float = 0.0):
+    """Per-pixel least-squares fit of log S(nu) = c + alpha u + beta u^2,
+    u = log(nu / nu0), over the bands of cube [L, N, N] (FP64, numpy lstsq).
+    Pixels with any S <= floor get NaN.  Returns (c, alpha, beta), each [N, N]."""
+    cube = np.asarray(cube, dtype=np.float64)
+    nu = np.asarray(nu, dtype=np.float64)
+    L, N = cube.shape[0], cube.shape[-1]
+    u = np.log(nu / (nu[0] if nu0 is None else nu0))
+    A = np.stack([np.ones(L), u, u * u], axis=1)
+    ok = np.all(cube > floor, axis=0)
+    logs = np.log(np.where(cube > 0, cube, 1.0)).reshape(L, N * N)
+    coef = np.linalg.lstsq(A, logs, rcond=None)[0].reshape(3, N, N)
+    coef[:, ~ok] = np.nan
+    return coef[0], coef[1], coef[2]

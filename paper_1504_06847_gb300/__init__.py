@@ -24,7 +24,7 @@ EXPORTS = ["mf_params_default", "mf_plan_create", "mf_plan_create_f64", "mf_plan
            "mf_plan_set_array", "mf_plan_get_state", "mf_plan_set_state", "mf_plan_get_report",
            "mf_wavelet_filter", "mf_status_string", "mf_plan_set_timing", "mf_plan_get_timing",
            "mf_kernel_name", "mf_xstep_noalloc", "mf_plan_set_option", "mf_batch_iterate",
-           "mf_admm_backward", "mf_plan_clear_status"]
+           "mf_admm_backward", "mf_plan_clear_status", "mf_spectral_index"]
 MF_OPT_WAV_TILE, MF_OPT_TEST_TC_STALL = 0, 1
 
 KERNELS = ["rows_fwd", "cols_solve", "rows_inv", "spectral", "wav_ll", "wav_level1", "wav_levelj", "setup",
@@ -111,6 +111,9 @@ def lib():
         L.mf_admm_backward.restype = ctypes.c_int
         L.mf_plan_set_option.argtypes = [vp, ctypes.c_int, ctypes.c_int]
         L.mf_plan_set_option.restype = ctypes.c_int
+        L.mf_spectral_index.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_double, ctypes.c_float, vp, vp, vp, vp]
+        L.mf_spectral_index.restype = ctypes.c_int
         L.mf_plan_clear_status.argtypes = [vp]
         L.mf_plan_clear_status.restype = ctypes.c_int
         L.mf_xstep_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.POINTER(Params), vp]
@@ -167,6 +170,30 @@ def batch_iterate(plans, ys, n_iter: int, **kw):
     _check(lib().mf_batch_iterate(hp, yp, len(plans), ctypes.byref(prm), int(n_iter)), "mf_batch_iterate")
     for p_, y in zip(plans, ys):
         p_._y_keepalive = y
+
+
+def spectral_index(cube, nu, nu0=None, floor=0.0, stream=None):
+    """Per-pixel fit log S = c + alpha u + beta u^2, u = log(nu/nu0), of a float32
+    CUDA cube [L, N, N] (see mf_spectral_index).  nu: L frequencies; nu0
+    defaults to nu[0].  Returns (c, alpha, beta) as float32 CUDA tensors [N, N]
+    (NaN where some S(nu_l) <= floor)."""
+    import torch
+
+    if cube.dtype != torch.float32 or not cube.is_cuda or cube.dim() != 3 or cube.shape[1] != cube.shape[2]:
+        raise ValueError("cube must be a float32 CUDA tensor [L, N, N]")
+    cube = cube.contiguous()
+    L_, N_ = int(cube.shape[0]), int(cube.shape[1])
+    if len(nu) != L_:
+        raise ValueError("one frequency per band")
+    nu_c = (ctypes.c_double * L_)(*[float(v) for v in nu])
+    nu0 = float(nu[0] if nu0 is None else nu0)
+    outs = [torch.empty((N_, N_), dtype=torch.float32, device=cube.device) for _ in range(3)]
+    with torch.cuda.device(cube.device):
+        s = torch.cuda.current_stream(cube.device).cuda_stream if stream is None else stream
+        _check(lib().mf_spectral_index(N_, L_, ctypes.c_void_p(cube.data_ptr()), nu_c, nu0, float(floor),
+                                       *[ctypes.c_void_p(o.data_ptr()) for o in outs], ctypes.c_void_p(s)),
+               "mf_spectral_index")
+    return tuple(outs)
 
 
 def xstep_noalloc(psf, y, b, x_out, **kw):

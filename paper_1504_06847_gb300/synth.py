@@ -86,6 +86,14 @@ def make_cube(N: int, L: int, n_sources: int, n_antennas: int, seed: int,
                 np.add.at(img, (ry[:, None], rx[None, :]), g)
                 sky += spec[:, None, None] * img[None]
 
+    return observe(sky, nu, nu0, n_antennas, rng, snr_db)
+
+
+def observe(sky: np.ndarray, nu: np.ndarray, nu0: float, n_antennas: int, rng, snr_db: float = 20.0) -> Cube:
+    """Steps 3-4 of the recipe for a given sky [L][N][N] at frequencies nu (GHz):
+    the disk array drawn from rng, the per-band PSFs (baselines scaled by
+    nu/nu0) and the dirty cube with white noise at snr_db."""
+    L, N = sky.shape[0], sky.shape[-1]
     r = np.sqrt(rng.uniform(0.0, 1.0, size=n_antennas))
     th = rng.uniform(0.0, 2.0 * np.pi, size=n_antennas)
     pos = np.stack([r * np.cos(th), r * np.sin(th)], axis=1)
@@ -143,3 +151,24 @@ def batch_workload(count: int = 16, seed: int = 400, n_antennas: int = 256):
     return [make_cube(N, L, n_sources=max(2, int(40 * (N / 256) ** 2)), n_antennas=n_antennas, seed=seed + i)
             for i, (N, L) in enumerate(batch_shapes(count, seed))]
 
+
+
+def two_gaussians(N: int = 256, L: int = 15, sigma_px: float = 12.0, n_antennas: int = 64, seed: int = 108,
+                  snr_db: float = 20.0) -> Cube:
+    """The two-Gaussian sky of the paper's first simulation (Section 4): two
+    overlapping Gaussian profiles centred at pixels 108 and 148 of the middle
+    row (of a 256-pixel image; scaled with N), peak 1 at the first band, with
+    constant spectral indices -1 and +1, over L bands from 1.025 GHz in 50 MHz
+    steps (nu0 = 1.025 GHz), observed with the disk-array PSFs of the recipe.
+    The paper gives no width: sigma_px (12 px) makes the profiles overlap
+    (each is at a quarter of its peak at the midpoint)."""
+    rng = np.random.default_rng(seed)
+    nu = 1.025 + 0.05 * np.arange(L)
+    nu0 = float(nu[0])
+    centres = [(N // 2, 108.0 * N / 256.0, -1.0), (N // 2, 148.0 * N / 256.0, 1.0)]
+    yy, xx = np.mgrid[0:N, 0:N]
+    sky = np.zeros((L, N, N))
+    for cy, cx, alpha in centres:
+        g = np.exp(-0.5 * (((yy - cy) ** 2 + (xx - cx) ** 2) / sigma_px ** 2))
+        sky += (nu / nu0)[:, None, None] ** alpha * g[None]
+    return observe(sky, nu, nu0, n_antennas, rng, snr_db)
