@@ -62,6 +62,15 @@ def lib():
             L.orc_iterate.argtypes = ([c_int, c_int, c_int, c_int, ip, dp, dp] + [dp] * 5 +
                                       [dp] * 9 + [c_int, dp])
             L.orc_iterate.restype = c_int
+            L.orc_linear_setup.argtypes = [c_int, c_int, dp, dp, dp, dp, dp]
+            L.orc_linear_setup.restype = c_int
+            L.orc_linear_apply.argtypes = [c_int, c_int, dp, dp, dp, dp, c_int]
+            L.orc_linear_apply.restype = None
+            L.orc_solve_cg.argtypes = [c_int, c_int, c_int, c_int, ip, dp, dp, dp, dp, c_int, dp, dp]
+            L.orc_solve_cg.restype = c_int
+            L.orc_iterate_linear.argtypes = ([c_int, c_int, c_int, c_int, ip, dp, dp, dp, dp, dp, c_int, dp] +
+                                             [dp] * 9 + [c_int, dp])
+            L.orc_iterate_linear.restype = c_int
             _lib = L
     return _lib
 
@@ -116,9 +125,15 @@ PARAM_ORDER = ("mu_eps", "mu_s", "mu_nu", "rho_P", "rho_T", "rho_V", "rho_S")
 
 
 class Problem:
-    """A cube (psf, y) with its regularisation, dictionary and level count."""
+    """A cube (psf, y) with its regularisation, dictionary and level count.
 
-    def __init__(self, psf, y, params: dict, J: int = 3, mask: int = 0x1FF, bases=None):
+    conv="circular" (the workloads): H is the circular convolution and step I
+    the Fourier filter.  conv="linear": H is the linear ("same"-size)
+    convolution by the PSF and step I runs cg_iters conjugate gradient
+    iterations per band from the previous X."""
+
+    def __init__(self, psf, y, params: dict, J: int = 3, mask: int = 0x1FF, bases=None, conv: str = "circular",
+                 cg_iters: int = 0):
         self.psf = np.ascontiguousarray(psf, dtype=np.float64)
         self.y = np.ascontiguousarray(y, dtype=np.float64)
         self.L, self.N = self.y.shape[0], self.y.shape[-1]
@@ -133,11 +148,20 @@ class Problem:
         self.params = dict(params)
         self.prm = np.array([float(self.params[k]) for k in PARAM_ORDER])
         shp = (self.L, self.N, self.N)
-        self.hre, self.him = np.empty(shp), np.empty(shp)
-        self.yre, self.yim = np.empty(shp), np.empty(shp)
+        if conv not in ("circular", "linear"):
+            raise ValueError(conv)
+        self.conv, self.cg_iters = conv, int(cg_iters)
         self.HtY = np.empty(shp)
-        rc = lib().orc_setup(self.N, self.L, _p(self.psf), _p(self.y), _p(self.hre), _p(self.him),
-                             _p(self.yre), _p(self.yim), _p(self.HtY))
+        if conv == "linear":
+            shp2 = (self.L, 2 * self.N, 2 * self.N)
+            self.h2re, self.h2im = np.empty(shp2), np.empty(shp2)
+            rc = lib().orc_linear_setup(self.N, self.L, _p(self.psf), _p(self.y), _p(self.h2re), _p(self.h2im),
+                                        _p(self.HtY))
+        else:
+            self.hre, self.him = np.empty(shp), np.empty(shp)
+            self.yre, self.yim = np.empty(shp), np.empty(shp)
+            rc = lib().orc_setup(self.N, self.L, _p(self.psf), _p(self.y), _p(self.hre), _p(self.him),
+                                 _p(self.yre), _p(self.yim), _p(self.HtY))
         assert rc == 0
 
     @property
@@ -160,11 +184,14 @@ class Problem:
         Returns the per-iteration history array [n_iter, NHIST] (or None)."""
         H = np.zeros((n_iter, NHIST)) if hist else None
         s = state
-        rc = lib().orc_iterate(*self._hdr(), _p(self.hre), _p(self.him), _p(self.yre),
-                               _p(self.yim), _p(self.HtY), _p(s["X"]), _p(s["P"]), _p(s["T"]),
-                               _p(s["V"]), _p(s["S"]), _p(s["GP"]), _p(s["GT"]), _p(s["GV"]),
-                               _p(s["GS"]), int(n_iter),
-                               _p(H) if hist else ctypes.POINTER(ctypes.c_double)())
+        arrays = [_p(s[k]) for k in ("X", "P", "T", "V", "S", "GP", "GT", "GV", "GS")]
+        hp = _p(H) if hist else ctypes.POINTER(ctypes.c_double)()
+        if self.conv == "linear":
+            rc = lib().orc_iterate_linear(*self._hdr(), _p(self.h2re), _p(self.h2im), _p(self.y), self.cg_iters,
+                                          _p(self.HtY), *arrays, int(n_iter), hp)
+        else:
+            rc = lib().orc_iterate(*self._hdr(), _p(self.hre), _p(self.him), _p(self.yre),
+                                   _p(self.yim), _p(self.HtY), *arrays, int(n_iter), hp)
         assert rc == 0
         return H
 
@@ -173,13 +200,28 @@ class Problem:
         H = self.iterate(st, n_iter, hist)
         return st, H
 
-    def solve(self, b: np.ndarray) -> np.ndarray:
-        """Step I alone: X = Q^-1 b, with b the full right-hand side of Eq. matB."""
+    def solve(self, b: np.ndarray, x0: np.ndarray | None = None, cg_iters: int | None = None) -> np.ndarray:
+        """Step I alone, b the full right-hand side of Eq. matB: X = Q^-1 b by the
+        Fourier filter (circular H), or cg_iters conjugate gradient iterations
+        from x0 (default 0) for the linear H."""
         b = np.ascontiguousarray(b, dtype=np.float64)
-        X = np.empty_like(b)
-        rc = lib().orc_solve(*self._hdr(), _p(self.hre), _p(self.him), _p(b), _p(X))
+        if self.conv == "linear":
+            X = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64, order="C")
+            it = self.cg_iters if cg_iters is None else int(cg_iters)
+            rc = lib().orc_solve_cg(*self._hdr(), _p(self.h2re), _p(self.h2im), it, _p(b), _p(X))
+        else:
+            X = np.empty_like(b)
+            rc = lib().orc_solve(*self._hdr(), _p(self.hre), _p(self.him), _p(b), _p(X))
         assert rc == 0
         return X
+
+    def apply_H(self, x: np.ndarray, adjoint: bool = False) -> np.ndarray:
+        """H x (or H^T x) of the linear convolution, for every band."""
+        assert self.conv == "linear"
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        out = np.empty_like(x)
+        lib().orc_linear_apply(self.N, self.L, _p(self.h2re), _p(self.h2im), _p(x), _p(out), int(adjoint))
+        return out
 
     def make_b(self, st: dict) -> np.ndarray:
         """Eq. matB from a state."""

@@ -357,6 +357,173 @@ static void solve_x(const problem* pb, const double* hre, const double* him,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Step I for a non-circulant H: linear convolution and conjugate gradients. */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Reading for a PSF that does not wrap around the image: H_l is the linear
+ * ("same"-size) 2-D convolution
+ *   (H x)[i] = sum_{j in [0,N)^2} psf[i - j + (N/2, N/2)] x[j],  psf = 0 outside [0,N)^2,
+ * and Q_l = H_l^T H_l + rho I is no longer a convolution, so step I is solved
+ * with the conjugate gradient algorithm that Algorithm 1's comment names
+ * (Hestenes-Stiefel), one system per band, started from the previous X and
+ * run for a fixed number of iterations.  H and H^T are applied exactly through
+ * a 2N x 2N FFT: with x embedded at [0,N)^2 and the PSF at offsets
+ * (u - N/2) mod 2N, the circular convolution of size 2N has no wrap-around on
+ * the cropped [0,N)^2 output.
+ */
+typedef struct {
+  const double* h2re;  /* [L][2N][2N] transfer function of the embedded PSF */
+  const double* h2im;
+  const double* y;     /* dirty cube [L][N][N], for the data-fit term */
+  int cg_iters;
+} lin_op;
+
+/* out = H x (adjoint = 0) or H^T x (adjoint = 1) for one band; buffers re, im hold (2N)^2 each. */
+static void lin_apply_band(int N, const double* h2re, const double* h2im, const double* x, double* out, int adjoint,
+                           double* re, double* im, const double* twr, const double* twi, double* lr, double* li) {
+  int M = 2 * N;
+  long MM = (long)M * M;
+  for (long i = 0; i < MM; i++) { re[i] = 0.0; im[i] = 0.0; }
+  for (int r = 0; r < N; r++)
+    for (int c = 0; c < N; c++) re[(long)r * M + c] = x[(long)r * N + c];
+  fft2_image(re, im, M, 0, twr, twi, lr, li);
+  for (long i = 0; i < MM; i++) {
+    double hr = h2re[i], hi = adjoint ? -h2im[i] : h2im[i];
+    double vr = re[i] * hr - im[i] * hi;
+    double vi = re[i] * hi + im[i] * hr;
+    re[i] = vr;
+    im[i] = vi;
+  }
+  fft2_image(re, im, M, 1, twr, twi, lr, li);
+  for (int r = 0; r < N; r++)
+    for (int c = 0; c < N; c++) out[(long)r * N + c] = re[(long)r * M + c] / (double)MM;
+}
+
+/* Transfer functions of the embedded PSFs and H^T y. */
+int orc_linear_setup(int N, int L, const double* psf, const double* y, double* h2re, double* h2im, double* HtY) {
+  int M = 2 * N;
+  long MM = (long)M * M, NN = (long)N * N;
+  for (long i = 0; i < MM * L; i++) { h2re[i] = 0.0; h2im[i] = 0.0; }
+  for (int l = 0; l < L; l++)
+    for (int u = 0; u < N; u++)
+      for (int v = 0; v < N; v++) {
+        int r = ((u - N / 2) % M + M) % M, c = ((v - N / 2) % M + M) % M;
+        h2re[l * MM + (long)r * M + c] = psf[l * NN + (long)u * N + v];
+      }
+  orc_fft2(h2re, h2im, M, L, -1);
+  double* twr = malloc(sizeof(double) * (M / 2 + 1));
+  double* twi = malloc(sizeof(double) * (M / 2 + 1));
+  twiddles(M, twr, twi);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int l = 0; l < L; l++) {
+    double *re = malloc(sizeof(double) * MM), *im = malloc(sizeof(double) * MM);
+    double *lr = malloc(sizeof(double) * M), *li = malloc(sizeof(double) * M);
+    lin_apply_band(N, h2re + l * MM, h2im + l * MM, y + l * NN, HtY + l * NN, 1, re, im, twr, twi, lr, li);
+    free(re); free(im); free(lr); free(li);
+  }
+  free(twr); free(twi);
+  return 0;
+}
+
+/* H x (adjoint 0) or H^T x (adjoint 1) for every band. */
+void orc_linear_apply(int N, int L, const double* h2re, const double* h2im, const double* x, double* out,
+                      int adjoint) {
+  int M = 2 * N;
+  long MM = (long)M * M, NN = (long)N * N;
+  double* twr = malloc(sizeof(double) * (M / 2 + 1));
+  double* twi = malloc(sizeof(double) * (M / 2 + 1));
+  twiddles(M, twr, twi);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int l = 0; l < L; l++) {
+    double *re = malloc(sizeof(double) * MM), *im = malloc(sizeof(double) * MM);
+    double *lr = malloc(sizeof(double) * M), *li = malloc(sizeof(double) * M);
+    lin_apply_band(N, h2re + l * MM, h2im + l * MM, x + l * NN, out + l * NN, adjoint, re, im, twr, twi, lr, li);
+    free(re); free(im); free(lr); free(li);
+  }
+  free(twr); free(twi);
+}
+
+static double dot(const double* a, const double* b, long n) {
+  double s = 0.0;
+  for (long i = 0; i < n; i++) s += a[i] * b[i];
+  return s;
+}
+
+/*
+ * Conjugate gradients on Q_l x_l = b_l, Q_l = H_l^T H_l + rho I, for every band,
+ * from the x given (updated in place), `iters` iterations:
+ *   r = b - Q x, p = r, g = r.r;
+ *   repeat: q = Q p, a = g / p.q, x += a p, r -= a q, g' = r.r, p = r + (g'/g) p, g = g'.
+ * A zero residual or a zero p.q ends the band's iterations (the system is solved).
+ * If dfit is not NULL it receives per band 1/2 ||y_l - H_l x_l||^2 for the final x.
+ */
+static void solve_cg(const problem* pb, const lin_op* lo, const double* b, double* X, double* dfit) {
+  int N = pb->N, L = pb->L, M = 2 * N;
+  long NN = (long)N * N, MM = (long)M * M;
+  double rho = pb->mu_eps + pb->rho_S + pb->rho_P + pb->nb * pb->rho_T; /* Eq. Qlsimp */
+  double* twr = malloc(sizeof(double) * (M / 2 + 1));
+  double* twi = malloc(sizeof(double) * (M / 2 + 1));
+  twiddles(M, twr, twi);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int l = 0; l < L; l++) {
+    const double* hr = lo->h2re + l * MM;
+    const double* hi = lo->h2im + l * MM;
+    double *re = malloc(sizeof(double) * MM), *im = malloc(sizeof(double) * MM);
+    double *lr = malloc(sizeof(double) * M), *li = malloc(sizeof(double) * M);
+    double *r = malloc(sizeof(double) * NN), *p = malloc(sizeof(double) * NN), *q = malloc(sizeof(double) * NN);
+    double* t = malloc(sizeof(double) * NN);
+    double* x = X + l * NN;
+    const double* bl = b + l * NN;
+    /* r = b - Q x */
+    lin_apply_band(N, hr, hi, x, t, 0, re, im, twr, twi, lr, li);
+    lin_apply_band(N, hr, hi, t, q, 1, re, im, twr, twi, lr, li);
+    for (long i = 0; i < NN; i++) {
+      r[i] = bl[i] - (q[i] + rho * x[i]);
+      p[i] = r[i];
+    }
+    double g = dot(r, r, NN);
+    for (int it = 0; it < lo->cg_iters && g > 0.0; it++) {
+      lin_apply_band(N, hr, hi, p, t, 0, re, im, twr, twi, lr, li);
+      lin_apply_band(N, hr, hi, t, q, 1, re, im, twr, twi, lr, li);
+      for (long i = 0; i < NN; i++) q[i] += rho * p[i];
+      double pq = dot(p, q, NN);
+      if (!(pq > 0.0)) break;
+      double a = g / pq;
+      for (long i = 0; i < NN; i++) {
+        x[i] += a * p[i];
+        r[i] -= a * q[i];
+      }
+      double g2 = dot(r, r, NN);
+      double beta = g2 / g;
+      for (long i = 0; i < NN; i++) p[i] = r[i] + beta * p[i];
+      g = g2;
+    }
+    if (dfit) {
+      lin_apply_band(N, hr, hi, x, t, 0, re, im, twr, twi, lr, li);
+      double f = 0.0;
+      for (long i = 0; i < NN; i++) {
+        double d = lo->y[l * NN + i] - t[i];
+        f += d * d;
+      }
+      dfit[l] = 0.5 * f;
+    }
+    free(re); free(im); free(lr); free(li); free(r); free(p); free(q); free(t);
+  }
+  free(twr); free(twi);
+}
+
+/* Step I alone with CG: X (in: start, out: result) for right-hand side b (including H^T y). */
+int orc_solve_cg(int N, int L, int J, int nb, const int* F, const double* h, const double* prm, const double* h2re,
+                 const double* h2im, int cg_iters, const double* b, double* X) {
+  problem pb;
+  if (load_problem(&pb, N, L, J, nb, F, h, prm)) return 1;
+  lin_op lo = {h2re, h2im, NULL, cg_iters};
+  solve_cg(&pb, &lo, b, X, NULL);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Steps II-VI.                                                              */
 /* ------------------------------------------------------------------------ */
 
@@ -488,10 +655,10 @@ static double sumsq_diff(const double* a, const double* b, long n) {
  * (d = change over the iteration; the residuals follow Boyd et al. for the
  * two-block split (X, V) | (P, T, S).)
  */
-int orc_iterate(int N, int L, int J, int nb, const int* F, const double* h, const double* prm,
-                const double* hre, const double* him, const double* yre, const double* yim,
-                const double* HtY, double* X, double* P, double* T, double* V, double* S,
-                double* GP, double* GT, double* GV, double* GS, int n_iter, double* hist) {
+static int iterate_impl(int N, int L, int J, int nb, const int* F, const double* h, const double* prm,
+                        const double* hre, const double* him, const double* yre, const double* yim, const lin_op* lo,
+                        const double* HtY, double* X, double* P, double* T, double* V, double* S, double* GP,
+                        double* GT, double* GV, double* GS, int n_iter, double* hist) {
   problem pb;
   if (load_problem(&pb, N, L, J, nb, F, h, prm)) return 1;
   if (L > 256) return 1;
@@ -516,7 +683,8 @@ int orc_iterate(int N, int L, int J, int nb, const int* F, const double* h, cons
       memcpy(GS0, GS, sizeof(double) * V_);
     }
     make_b(&pb, HtY, P, T, S, GP, GT, GS, b);
-    solve_x(&pb, hre, him, yre, yim, b, X, hist ? dfit : NULL);
+    if (lo) solve_cg(&pb, lo, b, X, hist ? dfit : NULL);
+    else solve_x(&pb, hre, him, yre, yim, b, X, hist ? dfit : NULL);
     primal_dual(&pb, X, P, T, V, S, GP, GT, GV, GS, Z);
     if (!hist) continue;
 
@@ -581,4 +749,25 @@ int orc_iterate(int N, int L, int J, int nb, const int* F, const double* h, cons
   free(b); free(Z); free(dfit); free(C);
   if (hist) { free(P0); free(T0); free(S0); free(GP0); free(GT0); free(GV0); free(GS0); }
   return 0;
+}
+
+/* Algorithm 1 with the circular H of the workloads: step I by the Fourier filter. */
+int orc_iterate(int N, int L, int J, int nb, const int* F, const double* h, const double* prm,
+                const double* hre, const double* him, const double* yre, const double* yim,
+                const double* HtY, double* X, double* P, double* T, double* V, double* S,
+                double* GP, double* GT, double* GV, double* GS, int n_iter, double* hist) {
+  return iterate_impl(N, L, J, nb, F, h, prm, hre, him, yre, yim, NULL, HtY, X, P, T, V, S, GP, GT, GV, GS, n_iter,
+                      hist);
+}
+
+/* Algorithm 1 with the linear H (see orc_linear_setup): step I by cg_iters conjugate
+ * gradient iterations per band from the previous X; the history's data-fit term
+ * is formed in the image domain. */
+int orc_iterate_linear(int N, int L, int J, int nb, const int* F, const double* h, const double* prm,
+                       const double* h2re, const double* h2im, const double* y, int cg_iters, const double* HtY,
+                       double* X, double* P, double* T, double* V, double* S, double* GP, double* GT, double* GV,
+                       double* GS, int n_iter, double* hist) {
+  lin_op lo = {h2re, h2im, y, cg_iters};
+  return iterate_impl(N, L, J, nb, F, h, prm, NULL, NULL, NULL, NULL, &lo, HtY, X, P, T, V, S, GP, GT, GV, GS, n_iter,
+                      hist);
 }

@@ -60,3 +60,19 @@ def dct_matrix(L: int) -> np.ndarray:
         for l in range(L):
             C[k, l] = a * np.cos(np.pi * (2 * l + 1) * k / (2 * L))
     return C
+
+
+def linear_conv_matrix(psf2d: np.ndarray) -> np.ndarray:
+    """H for one band with a PSF that does not wrap: (H x)[i] = sum_j psf[i - j + N/2] x[j]
+    in 2-D, the PSF taken as zero outside its N x N support (linear, "same"-size
+    convolution)."""
+    N = psf2d.shape[0]
+    H = np.zeros((N * N, N * N))
+    for r in range(N):
+        for c in range(N):
+            for rr in range(N):
+                for cc in range(N):
+                    u, v = r - rr + N // 2, c - cc + N // 2
+                    if 0 <= u < N and 0 <= v < N:
+                        H[r * N + c, rr * N + cc] = psf2d[u, v]
+    return H

@@ -31,9 +31,10 @@ from tests import _dense
 PRM = dict(mu_eps=0.003, mu_s=0.04, mu_nu=0.015, rho_P=0.7, rho_T=1.3, rho_V=1.9, rho_S=0.6)
 
 
-def _dense_ops(c, J, mask):
+def _dense_ops(c, J, mask, conv="circular"):
     L, N = c.y.shape[0], c.y.shape[-1]
-    H = [_dense.conv_matrix(c.psf[l]) for l in range(L)]
+    build = _dense.linear_conv_matrix if conv == "linear" else _dense.conv_matrix
+    H = [build(c.psf[l]) for l in range(L)]
     W = [_dense.dwt_matrix(h, N, J) for _, h in daubechies.dictionary(mask)]
     return H, W, _dense.dct_matrix(L)
 
@@ -70,11 +71,12 @@ def _reductions(c, H, W, C, prev, st, p):
     return {0: primal, 1: dual, 2: merit, 3: objective, 4: X.min(), 5: np.sum(X ** 2), 6: dgamma}
 
 
-@pytest.mark.parametrize("N,L,J,mask,seed", [(8, 4, 2, 0x1FF, 31), (16, 4, 3, 0x1FF, 32), (16, 3, 2, 0x0A5, 33)])
-def test_history_matches_dense_reductions(N, L, J, mask, seed):
+@pytest.mark.parametrize("N,L,J,mask,seed,conv", [(8, 4, 2, 0x1FF, 31, "circular"), (16, 4, 3, 0x1FF, 32, "circular"),
+                                                   (16, 3, 2, 0x0A5, 33, "circular"), (8, 3, 2, 0x1FF, 35, "linear")])
+def test_history_matches_dense_reductions(N, L, J, mask, seed, conv):
     c = synth.make_cube(N, L, n_sources=2, n_antennas=12, seed=seed)
-    pb = oracle.Problem(c.psf, c.y, PRM, J=J, mask=mask)
-    H, W, C = _dense_ops(c, J, mask)
+    pb = oracle.Problem(c.psf, c.y, PRM, J=J, mask=mask, conv=conv, cg_iters=4)
+    H, W, C = _dense_ops(c, J, mask, conv)
     st = pb.zero_state()
     for it in range(3):
         prev = {k: v.copy() for k, v in st.items()}
