@@ -117,6 +117,27 @@ def dct_matrix(L: int) -> np.ndarray:
     return C
 
 
+def chebyshev_matrix(L: int) -> np.ndarray:
+    """The Chebyshev polynomial basis of Section 4 made orthonormal on the L
+    equispaced bands: row k holds the degree-k polynomial of the family
+    orthonormal on t_l = -1 + 2l/(L-1) (the discrete Chebyshev, or Gram,
+    polynomials), with a positive leading coefficient.  Built by the
+    Stieltjes procedure with full re-orthogonalisation: p_0 = 1/sqrt(L),
+    p_k = t p_{k-1} minus its projections on p_0..p_{k-1}, normalised."""
+    t = np.linspace(-1.0, 1.0, L)
+    P = np.zeros((L, L))
+    P[0] = 1.0 / np.sqrt(L)
+    for k in range(1, L):
+        q = t * P[k - 1]
+        for _ in range(2):
+            q = q - P[:k].T @ (P[:k] @ q)
+        P[k] = q / np.linalg.norm(q)
+    return P
+
+
+SPECTRAL_BASES = {"dct": dct_matrix, "cheb": chebyshev_matrix}
+
+
 # ---------------------------------------------------------------------------
 # Problem and state
 # ---------------------------------------------------------------------------
@@ -133,7 +154,7 @@ class Problem:
     iterations per band from the previous X."""
 
     def __init__(self, psf, y, params: dict, J: int = 3, mask: int = 0x1FF, bases=None, conv: str = "circular",
-                 cg_iters: int = 0):
+                 cg_iters: int = 0, spectral=("dct",)):
         self.psf = np.ascontiguousarray(psf, dtype=np.float64)
         self.y = np.ascontiguousarray(y, dtype=np.float64)
         self.L, self.N = self.y.shape[0], self.y.shape[-1]
@@ -146,7 +167,13 @@ class Problem:
         for k, (_, h) in enumerate(self.bases):
             self.h[k, : len(h)] = h
         self.params = dict(params)
-        self.prm = np.array([float(self.params[k]) for k in PARAM_ORDER])
+        # spectral dictionary W_nu: a union of m_nu orthonormal bases (step V divides by m_nu rho_V + rho_S)
+        self.spectral = tuple(spectral)
+        self.mnu = len(self.spectral)
+        self.Cnu = [SPECTRAL_BASES[name](self.L) if isinstance(name, str) else np.asarray(name, dtype=np.float64)
+                    for name in self.spectral]
+        self.prm = np.concatenate([[float(self.params[k]) for k in PARAM_ORDER], [float(self.mnu)]] +
+                                  [C.ravel() for C in self.Cnu])
         shp = (self.L, self.N, self.N)
         if conv not in ("circular", "linear"):
             raise ValueError(conv)
@@ -174,7 +201,10 @@ class Problem:
 
     def zero_state(self) -> dict:
         shp = (self.L, self.N, self.N)
-        st = {k: np.zeros(shp) for k in ("X", "P", "V", "S", "GP", "GV", "GS")}
+        st = {k: np.zeros(shp) for k in ("X", "P", "S", "GP", "GS")}
+        vshp = shp if self.mnu == 1 else (self.mnu,) + shp
+        st["V"] = np.zeros(vshp)
+        st["GV"] = np.zeros(vshp)
         st["T"] = np.zeros((self.nb,) + shp)
         st["GT"] = np.zeros((self.nb,) + shp)
         return st

@@ -222,11 +222,19 @@ void orc_dct_matrix(int L, double* C) {
 /* Problem description.                                                      */
 /* ------------------------------------------------------------------------ */
 
+#define ORC_MAXNU 4
+
+/* The spectral dictionary W_nu is a union of m_nu orthonormal bases (Section
+ * 3, step V: W_nu W_nu^T = m_nu I): Cnu holds m_nu L x L matrices, basis j's
+ * coefficient k of a spectrum s being sum_l Cnu[(j L + k) L + l] s[l].  V and
+ * Gamma_V are [m_nu][L][N][N]. */
 typedef struct {
   int N, L, J, nb;
   int F[ORC_MAXB];
   double h[ORC_MAXB][ORC_MAXF];
   double mu_eps, mu_s, mu_nu, rho_P, rho_T, rho_V, rho_S;
+  int mnu;
+  const double* Cnu;
 } problem;
 
 static int load_problem(problem* pb, int N, int L, int J, int nb, const int* F,
@@ -240,6 +248,10 @@ static int load_problem(problem* pb, int N, int L, int J, int nb, const int* F,
   }
   pb->mu_eps = prm[0]; pb->mu_s = prm[1]; pb->mu_nu = prm[2];
   pb->rho_P = prm[3]; pb->rho_T = prm[4]; pb->rho_V = prm[5]; pb->rho_S = prm[6];
+  /* prm[7] = m_nu, then the m_nu spectral basis matrices (L x L each) */
+  pb->mnu = (int)prm[7];
+  if (pb->mnu < 1 || pb->mnu > ORC_MAXNU) return 1;
+  pb->Cnu = prm + 8;
   return 0;
 }
 
@@ -532,8 +544,6 @@ static void primal_dual(const problem* pb, const double* X, double* P, double* T
                         double* S, double* GP, double* GT, double* GV, double* GS, double* Z) {
   int N = pb->N, L = pb->L, nb = pb->nb;
   long NN = (long)N * N, V_ = NN * L;
-  double* C = malloc(sizeof(double) * L * L);
-  orc_dct_matrix(L, C);
 
   /* Step II: P <- max(0, X - Gamma_P / rho_P) */
 #pragma omp parallel for
@@ -555,25 +565,33 @@ static void primal_dual(const problem* pb, const double* X, double* P, double* T
     }
   }
 
-  /* Steps IV and V, one pixel spectrum at a time (uses the old S in IV). */
+  /* Steps IV and V, one pixel spectrum at a time (uses the old S in IV):
+   *   V_j = S_{mu_nu/rho_V}(S W_j - Gamma_Vj / rho_V) for every basis j,
+   *   S = (sum_j (Gamma_Vj + rho_V V_j) W_j^T - Gamma_S + rho_S X) / (m_nu rho_V + rho_S). */
   double tauV = pb->mu_nu / pb->rho_V;
-  double m_nu = 1.0;
+  int mnu = pb->mnu;
 #pragma omp parallel for schedule(static)
   for (long p = 0; p < NN; p++) {
     double s[256], u[256], v[256];
-    for (int k = 0; k < L; k++) {
-      double sw = 0.0;
-      for (int l = 0; l < L; l++) sw += C[k * L + l] * S[l * NN + p];
-      v[k] = soft(sw - GV[k * NN + p] / pb->rho_V, tauV);
-      V[k * NN + p] = v[k];
-    }
-    for (int l = 0; l < L; l++) {
-      double acc = 0.0;
-      for (int k = 0; k < L; k++) acc += C[k * L + l] * (GV[k * NN + p] + pb->rho_V * v[k]);
-      u[l] = acc;
+    for (int l = 0; l < L; l++) u[l] = 0.0;
+    for (int j = 0; j < mnu; j++) {
+      const double* C = pb->Cnu + (long)j * L * L;
+      const double* GVj = GV + (long)j * V_;
+      double* Vj = V + (long)j * V_;
+      for (int k = 0; k < L; k++) {
+        double sw = 0.0;
+        for (int l = 0; l < L; l++) sw += C[k * L + l] * S[l * NN + p];
+        v[k] = soft(sw - GVj[k * NN + p] / pb->rho_V, tauV);
+        Vj[k * NN + p] = v[k];
+      }
+      for (int l = 0; l < L; l++) {
+        double acc = 0.0;
+        for (int k = 0; k < L; k++) acc += C[k * L + l] * (GVj[k * NN + p] + pb->rho_V * v[k]);
+        u[l] += acc;
+      }
     }
     for (int l = 0; l < L; l++)
-      s[l] = (u[l] - GS[l * NN + p] + pb->rho_S * X[l * NN + p]) / (m_nu * pb->rho_V + pb->rho_S);
+      s[l] = (u[l] - GS[l * NN + p] + pb->rho_S * X[l * NN + p]) / ((double)mnu * pb->rho_V + pb->rho_S);
     for (int l = 0; l < L; l++) S[l * NN + p] = s[l];
   }
 
@@ -587,13 +605,15 @@ static void primal_dual(const problem* pb, const double* X, double* P, double* T
   for (long i = 0; i < V_ * nb; i++) GT[i] += pb->rho_T * (T[i] - Z[i]);
 #pragma omp parallel for schedule(static)
   for (long p = 0; p < NN; p++) {
-    for (int k = 0; k < L; k++) {
-      double sw = 0.0;
-      for (int l = 0; l < L; l++) sw += C[k * L + l] * S[l * NN + p];
-      GV[k * NN + p] += pb->rho_V * (V[k * NN + p] - sw);
+    for (int j = 0; j < mnu; j++) {
+      const double* C = pb->Cnu + (long)j * L * L;
+      for (int k = 0; k < L; k++) {
+        double sw = 0.0;
+        for (int l = 0; l < L; l++) sw += C[k * L + l] * S[l * NN + p];
+        GV[(long)j * V_ + k * NN + p] += pb->rho_V * (V[(long)j * V_ + k * NN + p] - sw);
+      }
     }
   }
-  free(C);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -646,7 +666,7 @@ static double sumsq_diff(const double* a, const double* b, long n) {
  * per iteration, measured after the iteration's dual update:
  *   [0] primal residual^2  ||P-X||^2 + ||T-W_sX||^2 + ||V-SW_nu||^2 + ||S-X||^2
  *   [1] dual residual^2    ||rho_P dP + rho_T W_s^T dT + rho_S dS||^2 + rho_V^2 ||dS W_nu||^2
- *   [2] merit  rho_P||dP||^2 + rho_T||dT||^2 + (rho_V+rho_S)||dS||^2 + sum_c ||dGamma_c||^2/rho_c
+ *   [2] merit  rho_P||dP||^2 + rho_T||dT||^2 + (m_nu rho_V+rho_S)||dS||^2 + sum_c ||dGamma_c||^2/rho_c
  *   [3] objective  1/2||Y-HX||^2 + mu_eps/2||X||^2 + mu_s||W_sX||_1 + mu_nu||XW_nu||_1
  *   [4] min(X)
  *   [5] ||X||^2
@@ -662,24 +682,22 @@ static int iterate_impl(int N, int L, int J, int nb, const int* F, const double*
   problem pb;
   if (load_problem(&pb, N, L, J, nb, F, h, prm)) return 1;
   if (L > 256) return 1;
-  long NN = (long)N * N, V_ = NN * L, VT = V_ * nb;
+  long NN = (long)N * N, V_ = NN * L, VT = V_ * nb, VV = V_ * pb.mnu;
   double* b = malloc(sizeof(double) * V_);
   double* Z = malloc(sizeof(double) * VT);
   double* dfit = malloc(sizeof(double) * L);
   double *P0 = NULL, *T0 = NULL, *S0 = NULL, *GP0 = NULL, *GT0 = NULL, *GV0 = NULL, *GS0 = NULL;
-  double* C = malloc(sizeof(double) * L * L);
-  orc_dct_matrix(L, C);
   if (hist) {
     P0 = malloc(sizeof(double) * V_); T0 = malloc(sizeof(double) * VT);
     S0 = malloc(sizeof(double) * V_); GP0 = malloc(sizeof(double) * V_);
-    GT0 = malloc(sizeof(double) * VT); GV0 = malloc(sizeof(double) * V_);
+    GT0 = malloc(sizeof(double) * VT); GV0 = malloc(sizeof(double) * VV);
     GS0 = malloc(sizeof(double) * V_);
   }
   for (int it = 0; it < n_iter; it++) {
     if (hist) {
       memcpy(P0, P, sizeof(double) * V_); memcpy(T0, T, sizeof(double) * VT);
       memcpy(S0, S, sizeof(double) * V_); memcpy(GP0, GP, sizeof(double) * V_);
-      memcpy(GT0, GT, sizeof(double) * VT); memcpy(GV0, GV, sizeof(double) * V_);
+      memcpy(GT0, GT, sizeof(double) * VT); memcpy(GV0, GV, sizeof(double) * VV);
       memcpy(GS0, GS, sizeof(double) * V_);
     }
     make_b(&pb, HtY, P, T, S, GP, GT, GS, b);
@@ -692,13 +710,16 @@ static int iterate_impl(int N, int L, int J, int nb, const int* F, const double*
     for (int q = 0; q < ORC_NHIST; q++) hh[q] = 0.0;
     /* primal residual */
     double r2 = sumsq_diff(P, X, V_) + sumsq_diff(T, Z, VT) + sumsq_diff(S, X, V_);
-    for (long p = 0; p < NN; p++)
-      for (int k = 0; k < L; k++) {
-        double sw = 0.0;
-        for (int l = 0; l < L; l++) sw += C[k * L + l] * S[l * NN + p];
-        double d = V[k * NN + p] - sw;
-        r2 += d * d;
-      }
+    for (int j = 0; j < pb.mnu; j++) {
+      const double* C = pb.Cnu + (long)j * L * L;
+      for (long p = 0; p < NN; p++)
+        for (int k = 0; k < L; k++) {
+          double sw = 0.0;
+          for (int l = 0; l < L; l++) sw += C[k * L + l] * S[l * NN + p];
+          double d = V[(long)j * V_ + k * NN + p] - sw;
+          r2 += d * d;
+        }
+    }
     hh[0] = r2;
     /* dual residual: needs W_s^T dT */
     double s2 = 0.0, dS2 = 0.0;
@@ -721,32 +742,36 @@ static int iterate_impl(int N, int L, int J, int nb, const int* F, const double*
         for (long i = 0; i < NN; i++) s2 += acc[i] * acc[i];
       }
       free(u); free(w); free(acc); free(buf);
+      /* rho_V^2 sum_j ||dS W_j||^2 = m_nu rho_V^2 ||dS||^2 (orthonormal bases) */
       dS2 = sumsq_diff(S, S0, V_);
-      s2 += pb.rho_V * pb.rho_V * dS2;
+      s2 += pb.mnu * pb.rho_V * pb.rho_V * dS2;
     }
     hh[1] = s2;
     double dGP = sumsq_diff(GP, GP0, V_), dGT = sumsq_diff(GT, GT0, VT);
-    double dGV = sumsq_diff(GV, GV0, V_), dGS = sumsq_diff(GS, GS0, V_);
+    double dGV = sumsq_diff(GV, GV0, VV), dGS = sumsq_diff(GS, GS0, V_);
     hh[2] = pb.rho_P * sumsq_diff(P, P0, V_) + pb.rho_T * sumsq_diff(T, T0, VT) +
-            (pb.rho_V + pb.rho_S) * dS2 + dGP / pb.rho_P + dGT / pb.rho_T + dGV / pb.rho_V +
+            (pb.mnu * pb.rho_V + pb.rho_S) * dS2 + dGP / pb.rho_P + dGT / pb.rho_T + dGV / pb.rho_V +
             dGS / pb.rho_S;
     /* objective */
     double fit = 0.0, x2 = 0.0, l1s = 0.0, l1n = 0.0, xmin = X[0];
     for (int l = 0; l < L; l++) fit += dfit[l];
     for (long i = 0; i < V_; i++) { x2 += X[i] * X[i]; if (X[i] < xmin) xmin = X[i]; }
     for (long i = 0; i < VT; i++) l1s += fabs(Z[i]);
-    for (long p = 0; p < NN; p++)
-      for (int k = 0; k < L; k++) {
-        double xw = 0.0;
-        for (int l = 0; l < L; l++) xw += C[k * L + l] * X[l * NN + p];
-        l1n += fabs(xw);
-      }
+    for (int j = 0; j < pb.mnu; j++) {
+      const double* C = pb.Cnu + (long)j * L * L;
+      for (long p = 0; p < NN; p++)
+        for (int k = 0; k < L; k++) {
+          double xw = 0.0;
+          for (int l = 0; l < L; l++) xw += C[k * L + l] * X[l * NN + p];
+          l1n += fabs(xw);
+        }
+    }
     hh[3] = fit + 0.5 * pb.mu_eps * x2 + pb.mu_s * l1s + pb.mu_nu * l1n;
     hh[4] = xmin;
     hh[5] = x2;
     hh[6] = dGP + dGT + dGV + dGS;
   }
-  free(b); free(Z); free(dfit); free(C);
+  free(b); free(Z); free(dfit);
   if (hist) { free(P0); free(T0); free(S0); free(GP0); free(GT0); free(GV0); free(GS0); }
   return 0;
 }

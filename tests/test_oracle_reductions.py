@@ -51,21 +51,25 @@ def _spectral(C, cube):
 
 
 def _reductions(c, H, W, C, prev, st, p):
-    X, P, T, V, S = st["X"], st["P"], st["T"], st["V"], st["S"]
+    """C: the spectral basis matrix, or a list of them (a union of bases)."""
+    Cs = C if isinstance(C, list) else [C]
+    X, P, T, S = st["X"], st["P"], st["T"], st["S"]
+    V = st["V"] if len(Cs) > 1 else [st["V"]]
     Z = [_apply_bands(Wk, X) for Wk in W]
     primal = (np.sum((P - X) ** 2) + sum(np.sum((T[k] - Z[k]) ** 2) for k in range(len(W)))
-              + np.sum((V - _spectral(C, S)) ** 2) + np.sum((S - X) ** 2))
+              + sum(np.sum((V[j] - _spectral(Cj, S)) ** 2) for j, Cj in enumerate(Cs)) + np.sum((S - X) ** 2))
     dP, dS = P - prev["P"], S - prev["S"]
     sx = p["rho_P"] * dP + p["rho_S"] * dS
     for k, Wk in enumerate(W):
         sx = sx + p["rho_T"] * _apply_bands(Wk.T, T[k] - prev["T"][k])
-    dual = np.sum(sx ** 2) + p["rho_V"] ** 2 * np.sum(_spectral(C, dS) ** 2)
+    dual = np.sum(sx ** 2) + p["rho_V"] ** 2 * sum(np.sum(_spectral(Cj, dS) ** 2) for Cj in Cs)
     HX = np.stack([(H[l] @ X[l].ravel()).reshape(X.shape[1:]) for l in range(X.shape[0])])
     objective = (0.5 * np.sum((c.y - HX) ** 2) + 0.5 * p["mu_eps"] * np.sum(X ** 2)
-                 + p["mu_s"] * sum(np.abs(z).sum() for z in Z) + p["mu_nu"] * np.abs(_spectral(C, X)).sum())
+                 + p["mu_s"] * sum(np.abs(z).sum() for z in Z)
+                 + p["mu_nu"] * sum(np.abs(_spectral(Cj, X)).sum() for Cj in Cs))
     dgamma = sum(np.sum((st[g] - prev[g]) ** 2) for g in ("GP", "GT", "GV", "GS"))
     merit = (p["rho_P"] * np.sum(dP ** 2) + p["rho_T"] * np.sum((T - prev["T"]) ** 2)
-             + (p["rho_V"] + p["rho_S"]) * np.sum(dS ** 2)
+             + (len(Cs) * p["rho_V"] + p["rho_S"]) * np.sum(dS ** 2)
              + sum(np.sum((st[g] - prev[g]) ** 2) / p[r]
                    for g, r in (("GP", "rho_P"), ("GT", "rho_T"), ("GV", "rho_V"), ("GS", "rho_S"))))
     return {0: primal, 1: dual, 2: merit, 3: objective, 4: X.min(), 5: np.sum(X ** 2), 6: dgamma}
@@ -85,6 +89,20 @@ def test_history_matches_dense_reductions(N, L, J, mask, seed, conv):
         for q, v in ref.items():
             assert abs(hist[q] - v) <= 1e-12 * max(abs(v), 1e-300) + 1e-300, (it, q, hist[q], v)
         assert hist[1] > 0 and hist[0] > 0
+
+
+def test_history_with_two_spectral_bases():
+    c = synth.make_cube(8, 5, n_sources=2, n_antennas=12, seed=36)
+    pb = oracle.Problem(c.psf, c.y, PRM, J=2, spectral=("dct", "cheb"))
+    H, W, C = _dense_ops(c, 2, 0x1FF)
+    Cs = [C, oracle.chebyshev_matrix(5)]
+    st = pb.zero_state()
+    for it in range(3):
+        prev = {k: v.copy() for k, v in st.items()}
+        hist = pb.iterate(st, 1, hist=True)[0]
+        ref = _reductions(c, H, W, Cs, prev, st, PRM)
+        for q, v in ref.items():
+            assert abs(hist[q] - v) <= 1e-12 * max(abs(v), 1e-300) + 1e-300, (it, q, hist[q], v)
 
 
 def test_dual_residual_sees_each_term():
