@@ -338,6 +338,22 @@ def measure_forms(stream, xstep_ms=None):
                                  "voxel_it_per_s_forward_and_reverse": c.y.size * K / (t_bwd * 1e-3),
                                  "dtype": "f32"}
         plan.close()
+        # the paper's first simulation: 256 x 256 x 15, its settings, its 350 iterations
+        c = synth.two_gaussians()
+        plan_e1 = mf.Plan(torch.tensor(c.psf, dtype=torch.float32, device="cuda"))
+        y_e1 = torch.tensor(c.y, dtype=torch.float32, device="cuda")
+        kw_e1 = dict(synth.PAPER_PARAMS, stream=stream.cuda_stream)
+        plan_e1.iterate(y_e1, 3, **kw_e1)
+        s.record(stream)
+        plan_e1.iterate(y_e1, 350, **kw_e1)
+        e.record(stream)
+        stream.synchronize()
+        t_e1 = s.elapsed_time(e)
+        out["paper_e1_256x256x15"] = {"iters": 350, "ms": t_e1, "voxel_it_per_s": c.y.size * 350 / (t_e1 * 1e-3),
+                                      "params": "Section 4 settings", "dtype": "f32",
+                                      "note": "the paper reports about 1.5 h on 15 CPU cores for a 256x256x15 run "
+                                              "of 350 iterations"}
+        plan_e1.close()
     if xstep_ms is not None:
         out["xstep_vs_cufft"] = xstep_reference(stream, xstep_ms)
     return out

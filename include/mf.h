@@ -67,6 +67,12 @@ typedef struct {
                                         and on the last one */
   int warm_start;                    /* 0: zero state first (Algorithm 1); 1: continue */
   void* stream;                      /* cudaStream_t; NULL = legacy default stream */
+  int cg_iters;                      /* plans from mf_plan_create_linear: conjugate gradient
+                                        iterations of step I per band (>= 1, default 20) */
+  unsigned spectral_mask;            /* spectral dictionary W_nu, a union of orthonormal bases
+                                        (step V divides by m_nu rho_V + rho_S): bit 0 the DCT,
+                                        bit 1 the Chebyshev basis (mf_spectral_basis); default 1.
+                                        Masks with bit 1 need L <= 64 and MF_FP32 or MF_FP64. */
 } mf_params;
 
 /* Filled by mf_plan_get_report, FP64 sums over the cube, measured after the
@@ -92,7 +98,7 @@ typedef struct {
 } mf_report;
 
 /* Defaults: mu_eps 0.001, mu_s 0.05, mu_nu 0.01, all rho 1, J 3, mask 0x1FF,
- * MF_FP32, resid_every 0, warm_start 0, stream NULL. */
+ * MF_FP32, resid_every 0, warm_start 0, stream NULL, cg_iters 20, spectral_mask 1. */
 void mf_params_default(mf_params* p);
 
 /* Creates a plan for N x N x L cubes.  psf_cube: device [L][N][N] float; it is
@@ -102,6 +108,19 @@ void mf_params_default(mf_params* p);
 mf_status mf_plan_create(int N, int L, const float* psf_cube, mf_plan** out);
 /* Same with an FP64 plan (all cubes double). */
 mf_status mf_plan_create_f64(int N, int L, const double* psf_cube, mf_plan** out);
+
+/* An FP32 plan whose H_l is the LINEAR ("same"-size) convolution by each
+ * band's PSF -- (H x)[i] = sum_{j in [0,N)^2} psf[i - j + (N/2, N/2)] x[j], the
+ * PSF zero outside its N x N support, no wrap-around -- for which
+ * Q_l = H_l^T H_l + rho I (Eq. Qlsimp) is no longer a convolution.  Step I then
+ * runs prm->cg_iters conjugate gradient iterations per band (the solver that
+ * Algorithm 1's comment names), started from the previous X: H and H^T are
+ * applied exactly through 2N x 2N FFTs (zero padding).  Every other step is as
+ * in mf_plan_create; the report's data-fit term is formed in the image domain.
+ * N is a power of two in [16, 1024].  The plan holds 17 cubes more than a
+ * circular plan (transfer function and work arrays at 2N, the CG vectors).
+ * mf_admm_backward rejects it.  Errors: MF_ERR_INVALID, MF_ERR_OOM, MF_ERR_CUDA. */
+mf_status mf_plan_create_linear(int N, int L, const float* psf_cube, mf_plan** out);
 /* Frees everything the plan owns; NULL is a no-op.  Synchronises the device. */
 void mf_plan_destroy(mf_plan* p);
 size_t mf_plan_device_bytes(const mf_plan* p);
@@ -151,9 +170,10 @@ typedef enum {
   MF_ARR_GAMMA_V = 3,  /* Gamma_V (DCT domain) */
   MF_ARR_GAMMA_S_DCT = 4, /* Gamma_S W_nu */
   MF_ARR_B = 5,        /* right-hand side of Eq. matB without the H^T Y term */
-  MF_ARR_GAMMA_T = 6   /* Gamma_T: [nd][L][N][N], nd distinct bases in mask order
+  MF_ARR_GAMMA_T = 6,  /* Gamma_T: [nd][L][N][N], nd distinct bases in mask order
                           (Db1..Db8, Haar folded into Db1 when both are on),
                           each band in the in-place Mallat layout */
+  MF_ARR_GAMMA_V2 = 7  /* Gamma_V of the Chebyshev spectral basis (its coefficient domain) */
 } mf_array;
 
 /* Device-to-device copies of a state array (dst/src: device, plan's real
@@ -162,7 +182,7 @@ typedef enum {
 mf_status mf_plan_get_array(mf_plan* p, int which, void* dst, size_t* count);
 mf_status mf_plan_set_array(mf_plan* p, int which, const void* src, size_t count);
 
-/* Whole ADMM state (every array above) as one opaque device buffer for
+/* Whole ADMM state (every array above, Gamma_V2 included) as one opaque device buffer for
  * checkpoint and warm restart.  With buf == NULL *bytes receives the size. */
 mf_status mf_plan_get_state(mf_plan* p, void* buf, size_t* bytes);
 mf_status mf_plan_set_state(mf_plan* p, const void* buf, size_t bytes);
@@ -182,7 +202,8 @@ typedef enum {
   MF_K_SETUP = 7,      /* per-call constants: F(y), g, c; zeroing of the state */
   MF_K_REDUCE = 8,     /* FP64 fold of the residual partials */
   MF_K_DUAL = 9,       /* dual residual: snapshot before step I, reduction after the iteration */
-  MF_K_COUNT = 10
+  MF_K_CG = 10,        /* step I of a linear-convolution plan: conjugate gradients, 2N FFTs */
+  MF_K_COUNT = 11
 } mf_kernel;
 
 /* Per-kernel CUDA-event timing of the plan's launches on its stream (off by
@@ -217,6 +238,15 @@ mf_status mf_plan_set_option(mf_plan* p, int option, int value);
  * be inconsistent after such a failure: restart from the zero state
  * (warm_start = 0) or restore a saved state. */
 mf_status mf_plan_clear_status(mf_plan* p);
+
+/* Host copy (row-major L x L, double) of a basis of the spectral dictionary:
+ * MF_SPECTRAL_DCT, the orthonormal DCT-II (row k = frequency k), or
+ * MF_SPECTRAL_CHEBYSHEV, the Chebyshev polynomials Section 4 suggests, made
+ * orthonormal on the L equispaced bands (the discrete Chebyshev / Gram
+ * polynomials; row n = degree n, positive leading coefficient), computed as
+ * the eigenvectors of their difference equation.  2 <= L <= 64. */
+typedef enum { MF_SPECTRAL_DCT = 0, MF_SPECTRAL_CHEBYSHEV = 1 } mf_spectral;
+mf_status mf_spectral_basis(int kind, int L, double* out);
 
 /* Host copy of the library's low-pass filter DbK (K = 1..8, 2K taps, double),
  * built at load time from Daubechies' spectral factorisation. */

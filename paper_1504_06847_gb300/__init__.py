@@ -17,18 +17,20 @@ LIB_PATH = os.path.join(HERE, "libmf.so")
 MF_OK, MF_ERR_INVALID, MF_ERR_OOM, MF_ERR_CUDA, MF_ERR_TIMEOUT, MF_ERR_NONFINITE, MF_ERR_TOO_LARGE = range(7)
 XSTEP_NOALLOC_MAX_VOXELS = 1 << 19
 MF_FP32, MF_FP64, MF_FP32_DCT_SPLITBF16 = range(3)
-ARR_X, ARR_GAMMA_P, ARR_S_DCT, ARR_GAMMA_V, ARR_GAMMA_S_DCT, ARR_B, ARR_GAMMA_T = range(7)
+ARR_X, ARR_GAMMA_P, ARR_S_DCT, ARR_GAMMA_V, ARR_GAMMA_S_DCT, ARR_B, ARR_GAMMA_T, ARR_GAMMA_V2 = range(8)
+SPECTRAL_DCT, SPECTRAL_CHEBYSHEV = 0, 1
 
 EXPORTS = ["mf_params_default", "mf_plan_create", "mf_plan_create_f64", "mf_plan_destroy",
            "mf_plan_device_bytes", "mf_admm_iterate", "mf_admm_iterate_f64", "mf_plan_get_array",
            "mf_plan_set_array", "mf_plan_get_state", "mf_plan_set_state", "mf_plan_get_report",
            "mf_wavelet_filter", "mf_status_string", "mf_plan_set_timing", "mf_plan_get_timing",
            "mf_kernel_name", "mf_xstep_noalloc", "mf_plan_set_option", "mf_batch_iterate",
-           "mf_admm_backward", "mf_plan_clear_status", "mf_spectral_index"]
+           "mf_admm_backward", "mf_plan_clear_status", "mf_spectral_index", "mf_plan_create_linear",
+           "mf_spectral_basis"]
 MF_OPT_WAV_TILE, MF_OPT_TEST_TC_STALL = 0, 1
 
 KERNELS = ["rows_fwd", "cols_solve", "rows_inv", "spectral", "wav_ll", "wav_level1", "wav_levelj", "setup",
-           "reduce", "dual"]
+           "reduce", "dual", "cg"]
 
 
 class MFError(RuntimeError):
@@ -43,7 +45,8 @@ class Params(ctypes.Structure):
                 ("rho_S", ctypes.c_double), ("wavelet_levels", ctypes.c_int),
                 ("wavelet_mask", ctypes.c_uint), ("precision", ctypes.c_int),
                 ("resid_every", ctypes.c_int), ("warm_start", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("cg_iters", ctypes.c_int),
+                ("spectral_mask", ctypes.c_uint)]
 
 
 class Report(ctypes.Structure):
@@ -69,7 +72,7 @@ def lib():
         vp, sz = ctypes.c_void_p, ctypes.c_size_t
         L.mf_params_default.argtypes = [ctypes.POINTER(Params)]
         L.mf_params_default.restype = None
-        for name in ("mf_plan_create", "mf_plan_create_f64"):
+        for name in ("mf_plan_create", "mf_plan_create_f64", "mf_plan_create_linear"):
             f = getattr(L, name)
             f.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(vp)]
             f.restype = ctypes.c_int
@@ -91,6 +94,8 @@ def lib():
         L.mf_plan_set_state.restype = ctypes.c_int
         L.mf_plan_get_report.argtypes = [vp, ctypes.POINTER(Report)]
         L.mf_plan_get_report.restype = ctypes.c_int
+        L.mf_spectral_basis.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        L.mf_spectral_basis.restype = ctypes.c_int
         L.mf_wavelet_filter.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
         L.mf_wavelet_filter.restype = ctypes.c_int
         L.mf_status_string.argtypes = [ctypes.c_int]
@@ -147,6 +152,14 @@ def wavelet_filter(K: int):
     n = ctypes.c_int()
     _check(lib().mf_wavelet_filter(K, taps, ctypes.byref(n)), "mf_wavelet_filter")
     return [taps[i] for i in range(n.value)]
+
+
+def spectral_basis(kind: int, L: int):
+    """The library's L x L spectral basis (SPECTRAL_DCT or SPECTRAL_CHEBYSHEV), host doubles,
+    as a list of rows."""
+    out = (ctypes.c_double * (L * L))()
+    _check(lib().mf_spectral_basis(int(kind), int(L), out), "mf_spectral_basis")
+    return [[out[k * L + l] for l in range(L)] for k in range(L)]
 
 
 def batch_iterate(plans, ys, n_iter: int, **kw):
@@ -224,9 +237,11 @@ class Plan:
     """A plan for N x N x L cubes on the current CUDA device.
 
     psf: CUDA tensor [L, N, N] (float32, or float64 for an FP64 plan).
+    linear=True: H is the linear (zero-padded, non-circulant) convolution and
+    step I runs conjugate gradients (float32; see mf_plan_create_linear).
     """
 
-    def __init__(self, psf):
+    def __init__(self, psf, linear: bool = False):
         import torch
 
         if not psf.is_cuda or psf.dim() != 3 or psf.shape[1] != psf.shape[2]:
@@ -237,7 +252,10 @@ class Plan:
         self.L, self.N = int(psf.shape[0]), int(psf.shape[1])
         psf = psf.contiguous()
         h = ctypes.c_void_p()
-        create = lib().mf_plan_create if self.dtype == torch.float32 else lib().mf_plan_create_f64
+        if linear and self.dtype != torch.float32:
+            raise ValueError("linear-convolution plans are float32")
+        create = (lib().mf_plan_create_linear if linear else
+                  lib().mf_plan_create if self.dtype == torch.float32 else lib().mf_plan_create_f64)
         _check(create(self.N, self.L, ctypes.c_void_p(psf.data_ptr()), ctypes.byref(h)), "mf_plan_create")
         self._h = h
         self.device = psf.device

@@ -96,7 +96,7 @@ extern "C" mf_status mf_admm_backward(mf_plan* p, const float* y, const mf_param
   if (!p || !prm || !y || !dL_dX || !dL_dy || n_iter < 1) return MF_ERR_INVALID;
   if (p->dbl || prm->precision != MF_FP32 || prm->warm_start) return MF_ERR_INVALID;
   if (!(prm->rho_P == prm->rho_T && prm->rho_P == prm->rho_V && prm->rho_P == prm->rho_S)) return MF_ERR_INVALID;
-  if (p->L > 64) return MF_ERR_INVALID;
+  if (p->L > 64 || p->linear || prm->spectral_mask != 1) return MF_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)prm->stream;
   WavSet<float> ws;
   IterScalars<float> sc;

@@ -267,7 +267,8 @@ __global__ void __launch_bounds__(FFT_NT) k_rows_inv(const cx<R>* __restrict__ i
 // MODE 2 is MODE 1 plus the data-fit partials 1/2 ||y - H x||^2 (Parseval over the
 // half spectrum: interior columns count twice) read from hh/yh.
 // MODE 3 applies H (X = h B) and MODE 4 applies Q^-1 alone (X = g B): both serve
-// the backward pass.
+// the backward pass.  MODE 5 applies H^T (X = conj(h) B), for the conjugate
+// gradient step I of a linear convolution.
 // The filter is applied in place in shared memory.  Packed column 0 holds the
 // DC column (A) and the Nyquist column (B) as A + iB; unpacking row ky needs
 // row (N - ky) mod N, so one thread takes both rows of a mirror pair.
@@ -283,6 +284,7 @@ struct ColFilter {
   __device__ __forceinline__ cx<R> apply(cx<R> Z, size_t o, R N2, R& fit, R wfit) const {
     cx<R> Xh;
     if (MODE == 3) Xh = cscale<R>(cmul<R>(hh[o], Z), (R)1 / N2);
+    else if (MODE == 5) Xh = cscale<R>(cmul<R>(cconj<R>(hh[o]), Z), (R)1 / N2);
     else if (MODE == 4) Xh = cscale<R>(Z, gg[o]);
     else Xh = cadd<R>(cc[o], cscale<R>(Z, gg[o]));
     if (MODE == 2) {
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(COLS_NT, 2) k_cols(cx<R>* __restrict__ work, c
         asm volatile("prefetch.global.L2 [%0];" ::"l"(gg + o));
       }
       if (MODE == 4) asm volatile("prefetch.global.L2 [%0];" ::"l"(gg + o));
-      if (MODE == 2 || MODE == 3) asm volatile("prefetch.global.L2 [%0];" ::"l"(hh + o));
+      if (MODE == 2 || MODE == 3 || MODE == 5) asm volatile("prefetch.global.L2 [%0];" ::"l"(hh + o));
       if (MODE == 2) asm volatile("prefetch.global.L2 [%0];" ::"l"(yh + o));
     }
   }
@@ -453,6 +455,7 @@ static cudaError_t cols_n(cx<R>* work, int L, const cx<R>* tw, int mode, cx<R>* 
   if (mode == 1) return cols_mode<R, N, 1>(work, L, tw, om, on, cc, ccn, gg, ggn, hh, hhn, yh, yhn, partials, s);
   if (mode == 3) return cols_mode<R, N, 3>(work, L, tw, om, on, cc, ccn, gg, ggn, hh, hhn, yh, yhn, partials, s);
   if (mode == 4) return cols_mode<R, N, 4>(work, L, tw, om, on, cc, ccn, gg, ggn, hh, hhn, yh, yhn, partials, s);
+  if (mode == 5) return cols_mode<R, N, 5>(work, L, tw, om, on, cc, ccn, gg, ggn, hh, hhn, yh, yhn, partials, s);
   return cols_mode<R, N, 2>(work, L, tw, om, on, cc, ccn, gg, ggn, hh, hhn, yh, yhn, partials, s);
 }
 

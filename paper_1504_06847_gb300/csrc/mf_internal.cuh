@@ -17,10 +17,12 @@
 #define MF_MAX_L 128
 #define MF_NQ 16          // reduction quantities per block partial
 #define MF_AUX_GRID (152 * 8)  // largest grid of the grid-stride reduction kernels (dual residual)
+#define MF_CG_CHUNKS 64        // blocks per band of the conjugate-gradient reductions
 
 namespace mf {
 
 const double* filter_taps(int K);  // DbK low-pass, 2K taps (daub.cpp)
+void chebyshev_matrix(int L, double* out);  // orthonormal Chebyshev basis on L bands, row n = degree n
 
 template <class R> struct cx_t;
 template <> struct cx_t<float> { typedef float2 type; };
@@ -77,7 +79,10 @@ struct mf_plan {
   void* b;
   void* GP;
   void* Sd;          // S W_nu
-  void* GV;          // Gamma_V
+  void* GV;          // Gamma_V (DCT basis of the spectral dictionary)
+  void* GV2;         // Gamma_V of the Chebyshev basis (spectral_mask bit 1)
+  void* Mb2;         // L x L change of basis DCT domain -> Chebyshev basis (C2 C^T)
+  int spectral_mask; // spectral dictionary of the current call
   void* GSd;         // Gamma_S W_nu
   void* GT[2];       // Gamma_T ping-pong, [MF_MAX_BASES][L][N][N]
   int gt_cur;
@@ -103,6 +108,19 @@ struct mf_plan {
   int* err;          // device error word (bounded waits that expired)
   void* dual;        // dual-residual snapshots and work cubes (allocated on first use)
   size_t dual_bytes;
+  // linear convolution (plans from mf_plan_create_linear): step I by conjugate gradients
+  int linear;
+  void* h2;          // transfer function of the PSF embedded in 2N x 2N: [L][2N][N] complex
+  void* h2_nyq;      // its kx = N column: [L][2N] complex
+  void* tw2;         // twiddles of length 2N
+  void* work2;       // packed half spectrum at 2N: [L][2N][N] complex
+  void* big;         // real 2N x 2N images [L][2N][2N]
+  void* cgv;         // H^T y, r, p, q: 4 cubes
+  int cg_iters;      // conjugate gradient iterations of the current call
+  const void* y_cur; // dirty cube of the current call
+  double rho_bar;    // rho of Eq. Qlsimp for the current call
+  double* cgs;       // per band: gamma, p.q, alpha, beta, gamma' ([5][L])
+  double* cgpart;    // per band and chunk partial sums [L][MF_CG_CHUNKS]
   size_t total_bytes;
   cudaStream_t stream;
   mf_status status;
@@ -132,7 +150,8 @@ template <class R> cudaError_t launch_rows_fwd(const R* in, cx<R>* out, int N, i
 // Column pass on the packed half spectrum of L bands.  mode 0: forward transform only,
 // unpacked into (out_main, out_nyq).  mode 1: forward, X = c + g B, inverse, in place.
 // mode 2: mode 1 plus the data-fit partials from (hh, yh).  mode 3: X = hh B / N^2 (applies
-// H).  mode 4: X = g B (applies Q^-1 without the H^T y term).
+// H).  mode 4: X = g B (applies Q^-1 without the H^T y term).  mode 5: X = conj(hh) B / N^2
+// (applies H^T).
 template <class R> cudaError_t launch_cols(cx<R>* work, int N, int L, const cx<R>* tw, int mode,
                                            cx<R>* out_main, cx<R>* out_nyq,
                                            const cx<R>* cc, const cx<R>* cc_nyq,
@@ -153,6 +172,10 @@ template <class R> cudaError_t launch_spectral(const R* X, R* GP, R* Sd, R* GV, 
                                                const R* dctC, int N, int L, IterScalars<R> sc,
                                                double* partials, int resid, cudaStream_t s);
 template <class R> int spectral_blocks(int N, int L);
+// The spectral step with the Chebyshev basis in the dictionary (DCT too when dct_on), L <= 64.
+template <class R> cudaError_t launch_spectral_b2(const R* X, R* GP, R* Sd, R* GV, R* GV2, R* GSd, R* b,
+                                                  const R* dctC, const R* Mb, int dct_on, int N, int L,
+                                                  IterScalars<R> sc, double* partials, int resid, cudaStream_t s);
 
 // Wavelet analysis of the low-low band: LL_j (M/2 x M/2) from the M x M input.
 template <class R> cudaError_t launch_wav_ll(const R* in, size_t in_band_stride, size_t in_basis_stride,
@@ -184,6 +207,14 @@ cudaError_t upload_taps();
 template <class R> cudaError_t launch_shift_psf(const R* psf, R* out, int N, size_t total, cudaStream_t s);
 
 cudaError_t launch_finalize(const double* partials, int nblocks, double* sums, int accumulate, cudaStream_t s);
+
+// Step I of a linear-convolution plan (cg.cu): transfer function and twiddles at
+// 2N (plan creation), H^T y (per call), the conjugate gradient solve (per
+// iteration) and the data-fit partials 1/2 ||y - H X||^2 (residual iterations).
+cudaError_t linear_setup(mf_plan* p, const float* psf);
+cudaError_t linear_hty(mf_plan* p, const float* y, cudaStream_t s);
+cudaError_t linear_step_I(mf_plan* p, int cg_iters, double rho_bar, cudaStream_t s);
+cudaError_t linear_fit(mf_plan* p, const float* y, double* partials, int* nblocks, cudaStream_t s);
 
 // Dual residual of residual iterations (dual.cu): cubes of p->dual, the
 // snapshot taken before step I, and the reduction after the iteration.

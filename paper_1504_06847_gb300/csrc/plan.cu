@@ -91,9 +91,11 @@ struct Alloc {
 };
 
 void free_plan_memory(mf_plan* p) {
-  void* ptrs[] = {p->X, p->b, p->GP, p->Sd, p->GV, p->GSd, p->GT[0], p->GT[1], p->work, p->hhat, p->hhat_nyq,
+  void* ptrs[] = {p->X, p->b, p->GP, p->Sd, p->GV, p->GV2, p->Mb2, p->GSd, p->GT[0], p->GT[1], p->work, p->hhat,
+                  p->hhat_nyq,
                   p->yhat, p->yhat_nyq, p->cc, p->cc_nyq, p->gg, p->gg_nyq, p->tw, p->dctC, p->scratch,
-                  p->partials, p->sums, p->wset, p->dct_tc, p->err, p->bwd_buf, p->dual};
+                  p->partials, p->sums, p->wset, p->dct_tc, p->err, p->bwd_buf, p->dual, p->h2, p->h2_nyq,
+                  p->tw2, p->work2, p->big, p->cgv, p->cgs, p->cgpart};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   p->bwd_buf = nullptr;
@@ -136,6 +138,8 @@ mf_status create(int N, int L, const R* psf, mf_plan** out) {
   p->Sd = a.get(cb);
   p->GV = a.get(cb);
   p->GSd = a.get(cb);
+  p->GV2 = a.get(cb);
+  p->Mb2 = a.get(sizeof(R) * L * L);
   p->GT[0] = a.get(cb * MF_MAX_BASES);
   p->GT[1] = a.get(cb * MF_MAX_BASES);
   p->work = a.get(half);
@@ -162,6 +166,7 @@ mf_status create(int N, int L, const R* psf, mf_plan** out) {
   const size_t colblocks = (size_t)L * N;  // upper bound of the column kernel's grid
   if (colblocks > cap) cap = colblocks;
   if ((size_t)MF_AUX_GRID > cap) cap = MF_AUX_GRID;
+  if ((size_t)MF_CG_CHUNKS * L > cap) cap = (size_t)MF_CG_CHUNKS * L;  // data-fit partials of a linear plan
   p->partial_cap = cap;
   p->partials = (double*)a.get(cap * MF_NQ * sizeof(double));
   p->sums = (double*)a.get(MF_NQ * sizeof(double));
@@ -186,7 +191,22 @@ mf_status create(int N, int L, const R* psf, mf_plan** out) {
       const double ak = k == 0 ? std::sqrt(1.0 / L) : std::sqrt(2.0 / L);
       for (int l = 0; l < L; l++) C[k * L + l] = (R)(ak * std::cos(M_PI * (2.0 * l + 1.0) * k / (2.0 * L)));
     }
+    // change of basis from the DCT domain (where S and Gamma_S live) to the
+    // Chebyshev basis of the spectral dictionary: M = C2 C^T (offered for L <= 64)
+    std::vector<double> C2((size_t)L * L);
+    std::vector<R> Mh((size_t)L * L, (R)0);
+    if (L <= 64) chebyshev_matrix(L, C2.data());
+    for (int k2 = 0; k2 < L && L <= 64; k2++) {
+      for (int k1 = 0; k1 < L; k1++) {
+        const double ak = k1 == 0 ? std::sqrt(1.0 / L) : std::sqrt(2.0 / L);
+        long double acc = 0;
+        for (int l = 0; l < L; l++)
+          acc += (long double)C2[(size_t)k2 * L + l] * (ak * std::cos(M_PI * (2.0 * l + 1.0) * k1 / (2.0 * L)));
+        Mh[(size_t)k2 * L + k1] = (R)acc;
+      }
+    }
     cudaError_t e1 = cudaMemcpy(p->tw, tw, sizeof(cx<R>) * N, cudaMemcpyHostToDevice);
+    if (e1 == cudaSuccess) e1 = cudaMemcpy(p->Mb2, Mh.data(), sizeof(R) * L * L, cudaMemcpyHostToDevice);
     cudaError_t e2 = cudaMemcpy(p->dctC, C, sizeof(R) * L * L, cudaMemcpyHostToDevice);
     cudaError_t e3 = upload_taps();
     if (e3 == cudaSuccess) e3 = cudaMemset(p->err, 0, sizeof(int));
@@ -222,6 +242,7 @@ mf_status create(int N, int L, const R* psf, mf_plan** out) {
 }
 
 mf_status check_params(const mf_plan* p, const mf_params* prm, int n_iter, int want_dbl) {
+  if (p && prm && p->linear && n_iter >= 1 && prm->cg_iters < 1) return MF_ERR_INVALID;
   if (!p || !prm || n_iter < 1) return MF_ERR_INVALID;
   if (p->dbl != want_dbl) return MF_ERR_INVALID;
   if (!(prm->rho_P > 0 && prm->rho_T > 0 && prm->rho_V > 0 && prm->rho_S > 0)) return MF_ERR_INVALID;
@@ -232,6 +253,9 @@ mf_status check_params(const mf_plan* p, const mf_params* prm, int n_iter, int w
   if (J < 1 || (p->N >> J) < 2) return MF_ERR_INVALID;
   if (prm->wavelet_mask == 0 || (prm->wavelet_mask >> 9) != 0) return MF_ERR_INVALID;
   if (prm->resid_every < 0) return MF_ERR_INVALID;
+  if (p->linear && prm->cg_iters < 1) return MF_ERR_INVALID;
+  if (prm->spectral_mask < 1 || prm->spectral_mask > 3) return MF_ERR_INVALID;
+  if ((prm->spectral_mask & 2) && (p->L > 64 || prm->precision == MF_FP32_DCT_SPLITBF16)) return MF_ERR_INVALID;
   if (p->dbl) {
     if (prm->precision != MF_FP64) return MF_ERR_INVALID;
   } else if (prm->precision == MF_FP32_DCT_SPLITBF16) {
@@ -271,12 +295,21 @@ WavSet<R> make_wavset(unsigned mask, int* n_s) {
 
 template <class R>
 cudaError_t spectral_step(mf_plan* p, const IterScalars<R>& sc, int resid, int precision, cudaStream_t s) {
+  if (p->spectral_mask & 2)
+    return launch_spectral_b2<R>((const R*)p->X, (R*)p->GP, (R*)p->Sd, (R*)p->GV, (R*)p->GV2, (R*)p->GSd, (R*)p->b,
+                                 (const R*)p->dctC, (const R*)p->Mb2, p->spectral_mask & 1, p->N, p->L, sc,
+                                 p->partials, resid, s);
   return launch_spectral<R>((const R*)p->X, (R*)p->GP, (R*)p->Sd, (R*)p->GV, (R*)p->GSd, (R*)p->b,
                             (const R*)p->dctC, p->N, p->L, sc, p->partials, resid, s);
 }
 template <>
 cudaError_t spectral_step<float>(mf_plan* p, const IterScalars<float>& sc, int resid, int precision,
                                  cudaStream_t s) {
+  if (p->spectral_mask & 2)
+    return launch_spectral_b2<float>((const float*)p->X, (float*)p->GP, (float*)p->Sd, (float*)p->GV,
+                                     (float*)p->GV2, (float*)p->GSd, (float*)p->b, (const float*)p->dctC,
+                                     (const float*)p->Mb2, p->spectral_mask & 1, p->N, p->L, sc, p->partials, resid,
+                                     s);
   if (precision == MF_FP32_DCT_SPLITBF16)
     return launch_spectral_tc((const float*)p->X, (float*)p->GP, (float*)p->Sd, (float*)p->GV, (float*)p->GSd,
                               (float*)p->b, (const uint16_t*)p->dct_tc, p->N, p->L, sc, p->partials, resid, p->err,
@@ -287,7 +320,8 @@ cudaError_t spectral_step<float>(mf_plan* p, const IterScalars<float>& sc, int r
 
 template <class R>
 int spectral_grid(const mf_plan* p, int precision) {
-  return precision == MF_FP32_DCT_SPLITBF16 ? spectral_tc_blocks(p->N) : spectral_blocks<R>(p->N, p->L);
+  return (precision == MF_FP32_DCT_SPLITBF16 && !(p->spectral_mask & 2)) ? spectral_tc_blocks(p->N)
+                                                                        : spectral_blocks<R>(p->N, p->L);
 }
 
 template <class R>
@@ -302,6 +336,22 @@ cudaError_t iteration(mf_plan* p, int J, const WavSet<R>& ws, const WavSet<R>* w
     if ((e = dual_snapshot<R>(p, s))) return e;
   }
   // step I
+  if (p->linear) {
+    {
+      // conjugate gradients with the linear convolution, started from the previous X
+      Timed t(p, MF_K_CG, s);
+      if ((e = linear_step_I(p, p->cg_iters, p->rho_bar, s))) return e;
+    }
+    if (resid) {
+      int nb = 0;
+      {
+        Timed t(p, MF_K_CG, s);
+        if ((e = linear_fit(p, (const float*)p->y_cur, p->partials, &nb, s))) return e;
+      }
+      Timed t(p, MF_K_REDUCE, s);
+      if ((e = launch_finalize(p->partials, nb, p->sums, 0, s))) return e;
+    }
+  } else {
   {
     Timed t(p, MF_K_ROWS_FWD, s);
     if ((e = launch_rows_fwd<R>((const R*)p->b, (cx<R>*)p->work, N, N * L, (const cx<R>*)p->tw, s))) return e;
@@ -321,6 +371,7 @@ cudaError_t iteration(mf_plan* p, int J, const WavSet<R>& ws, const WavSet<R>* w
   {
     Timed t(p, MF_K_ROWS_INV, s);
     if ((e = launch_rows_inv<R>((const cx<R>*)p->work, (R*)p->X, N, N * L, (const cx<R>*)p->tw, s))) return e;
+  }
   }
   // steps II, IV, V (+ duals), pointwise part of b
   {
@@ -406,9 +457,13 @@ mf_status prepare(mf_plan* p, const R* y, const mf_params* prm, int n_iter, cuda
   sc.inv_rho_P = (R)(1.0 / prm->rho_P);
   sc.inv_rho_T = (R)(1.0 / prm->rho_T);
   sc.inv_rho_V = (R)(1.0 / prm->rho_V);
-  sc.inv_VS = (R)(1.0 / (prm->rho_V + prm->rho_S));
+  const int m_nu = (prm->spectral_mask & 1) + ((prm->spectral_mask >> 1) & 1);  // bases of W_nu
+  sc.inv_VS = (R)(1.0 / (m_nu * prm->rho_V + prm->rho_S));  // step V: m_nu rho_V + rho_S
   if (prm->warm_start && p->nd_state != ws.nd && p->iters_done > 0)
     return MF_ERR_INVALID;  // the stored Gamma_T belongs to another dictionary
+  if (prm->warm_start && p->iters_done > 0 && p->spectral_mask != (int)prm->spectral_mask)
+    return MF_ERR_INVALID;  // the stored Gamma_V belongs to another spectral dictionary
+  p->spectral_mask = (int)prm->spectral_mask;
   if (prm->resid_every > 0 && !p->dual) {
     // snapshots and work cubes of the dual residual, kept by the plan from now on
     const size_t bytes = dual_cubes() * p->cube * sizeof(R);
@@ -420,7 +475,14 @@ mf_status prepare(mf_plan* p, const R* y, const mf_params* prm, int n_iter, cuda
     p->dual_bytes = bytes;
   }
   cudaError_t e = cudaMemcpyAsync(p->wset, &ws, sizeof(ws), cudaMemcpyHostToDevice, s);
-  {
+  p->rho_bar = rho_bar;
+  p->cg_iters = prm->cg_iters;
+  p->y_cur = y;
+  if (p->linear) {
+    // H^T y of the linear convolution (step I runs conjugate gradients)
+    Timed t(p, MF_K_SETUP, s, 1);
+    if (!e) e = linear_hty(p, (const float*)y, s);
+  } else {
     // constants: F(y), g, c
     Timed t(p, MF_K_SETUP, s, 4);
     if (!e) e = launch_rows_fwd<R>(y, (cx<R>*)p->work, N, N * L, (const cx<R>*)p->tw, s);
@@ -431,9 +493,11 @@ mf_status prepare(mf_plan* p, const R* y, const mf_params* prm, int n_iter, cuda
       e = launch_constants<R>((const cx<R>*)p->hhat, (const cx<R>*)p->hhat_nyq, (const cx<R>*)p->yhat,
                               (const cx<R>*)p->yhat_nyq, (cx<R>*)p->cc, (cx<R>*)p->cc_nyq, (R*)p->gg,
                               (R*)p->gg_nyq, N, L, rho_bar, s);
+  }
+  {
     if (!e && !prm->warm_start) {
       const size_t cb = p->cube * sizeof(R);
-      void* z[] = {p->X, p->b, p->GP, p->Sd, p->GV, p->GSd};
+      void* z[] = {p->X, p->b, p->GP, p->Sd, p->GV, p->GV2, p->GSd};
       for (void* q : z)
         if (!e) e = cudaMemsetAsync(q, 0, cb, s);
       if (!e) e = cudaMemsetAsync(p->GT[p->gt_cur], 0, cb * MF_MAX_BASES, s);
@@ -584,6 +648,7 @@ void* array_ptr(mf_plan* p, int which, size_t* count) {
     case MF_ARR_S_DCT: return p->Sd;
     case MF_ARR_GAMMA_V: return p->GV;
     case MF_ARR_GAMMA_S_DCT: return p->GSd;
+    case MF_ARR_GAMMA_V2: return p->GV2;
     case MF_ARR_B: return p->b;
     case MF_ARR_GAMMA_T: *count = p->cube * (p->nd_state > 0 ? p->nd_state : MF_MAX_BASES); return p->GT[p->gt_cur];
     default: return nullptr;
@@ -624,6 +689,8 @@ void mf_params_default(mf_params* p) {
   p->wavelet_levels = 3;
   p->wavelet_mask = 0x1FF;
   p->precision = MF_FP32;
+  p->cg_iters = 20;
+  p->spectral_mask = 1;
 }
 
 mf_status mf_plan_create(int N, int L, const float* psf_cube, mf_plan** out) {
@@ -631,6 +698,37 @@ mf_status mf_plan_create(int N, int L, const float* psf_cube, mf_plan** out) {
 }
 mf_status mf_plan_create_f64(int N, int L, const double* psf_cube, mf_plan** out) {
   return create<double>(N, L, psf_cube, out);
+}
+
+mf_status mf_plan_create_linear(int N, int L, const float* psf_cube, mf_plan** out) {
+  if (!out) return MF_ERR_INVALID;
+  *out = nullptr;
+  if (!psf_cube || !is_pow2(N) || N < 16 || N > 1024 || L < 2 || L > MF_MAX_L) return MF_ERR_INVALID;
+  mf_plan* p = nullptr;
+  mf_status st = create<float>(N, L, psf_cube, &p);
+  if (st != MF_OK) return st;
+  const size_t cb = p->cube * sizeof(float);
+  Alloc a{p};
+  p->h2 = a.get(4 * cb);
+  p->h2_nyq = a.get((size_t)L * 2 * N * sizeof(cx<float>));
+  p->tw2 = a.get((size_t)2 * N * sizeof(cx<float>));
+  p->work2 = a.get(4 * cb);
+  p->big = a.get(4 * cb);
+  p->cgv = a.get(4 * cb);
+  p->cgs = (double*)a.get((size_t)5 * L * sizeof(double));
+  p->cgpart = (double*)a.get((size_t)MF_CG_CHUNKS * L * sizeof(double));
+  if (!a.ok) {
+    mf_plan_destroy(p);
+    return MF_ERR_OOM;
+  }
+  p->linear = 1;
+  if (linear_setup(p, psf_cube) != cudaSuccess) {
+    cudaGetLastError();
+    mf_plan_destroy(p);
+    return MF_ERR_CUDA;
+  }
+  *out = p;
+  return MF_OK;
 }
 
 void mf_plan_destroy(mf_plan* p) {
@@ -682,14 +780,14 @@ mf_status mf_plan_set_array(mf_plan* p, int which, const void* src, size_t count
 mf_status mf_plan_get_state(mf_plan* p, void* buf, size_t* bytes) {
   if (!p || !bytes) return MF_ERR_INVALID;
   const size_t cb = p->cube * p->esz;
-  const size_t need = cb * (6 + MF_MAX_BASES);
+  const size_t need = cb * (7 + MF_MAX_BASES);
   if (!buf) {
     *bytes = need;
     return MF_OK;
   }
   if (*bytes < need) return MF_ERR_INVALID;
   if (cudaStreamSynchronize(p->stream) != cudaSuccess) return MF_ERR_CUDA;
-  void* src[] = {p->X, p->b, p->GP, p->Sd, p->GV, p->GSd};
+  void* src[] = {p->X, p->b, p->GP, p->Sd, p->GV, p->GV2, p->GSd};
   char* d = (char*)buf;
   for (void* s : src) {
     if (cudaMemcpy(d, s, cb, cudaMemcpyDeviceToDevice) != cudaSuccess) return MF_ERR_CUDA;
@@ -703,9 +801,9 @@ mf_status mf_plan_get_state(mf_plan* p, void* buf, size_t* bytes) {
 mf_status mf_plan_set_state(mf_plan* p, const void* buf, size_t bytes) {
   if (!p || !buf) return MF_ERR_INVALID;
   const size_t cb = p->cube * p->esz;
-  if (bytes != cb * (6 + MF_MAX_BASES)) return MF_ERR_INVALID;
+  if (bytes != cb * (7 + MF_MAX_BASES)) return MF_ERR_INVALID;
   if (cudaStreamSynchronize(p->stream) != cudaSuccess) return MF_ERR_CUDA;
-  void* dst[] = {p->X, p->b, p->GP, p->Sd, p->GV, p->GSd};
+  void* dst[] = {p->X, p->b, p->GP, p->Sd, p->GV, p->GV2, p->GSd};
   const char* s = (const char*)buf;
   for (void* d : dst) {
     if (cudaMemcpy(d, s, cb, cudaMemcpyDeviceToDevice) != cudaSuccess) return MF_ERR_CUDA;
@@ -741,7 +839,8 @@ mf_status mf_plan_get_report(mf_plan* p, mf_report* r) {
     p->report.primal_res = q[Q_DGP] / (w[0] * w[0]) + q[Q_DGT] / (w[1] * w[1]) + q[Q_DGV] / (w[2] * w[2]) +
                            q[Q_DGS] / (w[3] * w[3]);
     p->report.dual_gamma = q[Q_DGP] + q[Q_DGT] + q[Q_DGV] + q[Q_DGS];
-    p->report.dual_res = q[Q_DUALX] + w[2] * w[2] * q[Q_DS2];
+    const int m_nu = (p->last_params.spectral_mask & 1) + ((p->last_params.spectral_mask >> 1) & 1);
+    p->report.dual_res = q[Q_DUALX] + m_nu * w[2] * w[2] * q[Q_DS2];  // rho_V^2 sum_j ||dS W_j||^2
     const mf_params* pr = &p->last_params;
     p->report.objective = q[Q_FIT] + 0.5 * pr->mu_eps * q[Q_X2] + pr->mu_s * q[Q_L1S] + pr->mu_nu * q[Q_L1NU];
     p->report.x_min = q[Q_XMIN];
@@ -804,8 +903,24 @@ mf_status mf_plan_clear_status(mf_plan* p) {
 
 const char* mf_kernel_name(int kernel) {
   static const char* names[MF_K_COUNT] = {"rows_fwd", "cols_solve", "rows_inv", "spectral", "wav_ll",
-                                          "wav_level1", "wav_levelj", "setup", "reduce", "dual"};
+                                          "wav_level1", "wav_levelj", "setup", "reduce", "dual", "cg"};
   return (kernel >= 0 && kernel < MF_K_COUNT) ? names[kernel] : "unknown";
+}
+
+mf_status mf_spectral_basis(int kind, int L, double* out) {
+  if (!out || L < 2 || L > 64) return MF_ERR_INVALID;
+  if (kind == MF_SPECTRAL_DCT) {
+    for (int k = 0; k < L; k++) {
+      const double ak = k == 0 ? std::sqrt(1.0 / L) : std::sqrt(2.0 / L);
+      for (int l = 0; l < L; l++) out[k * L + l] = ak * std::cos(M_PI * (2.0 * l + 1.0) * k / (2.0 * L));
+    }
+    return MF_OK;
+  }
+  if (kind == MF_SPECTRAL_CHEBYSHEV) {
+    chebyshev_matrix(L, out);
+    return MF_OK;
+  }
+  return MF_ERR_INVALID;
 }
 
 mf_status mf_wavelet_filter(int K, double* taps, int* len) {

@@ -202,6 +202,268 @@ __global__ void __launch_bounds__(SP_NT) k_spectral(const R* __restrict__ X, R* 
   }
 }
 
+// The spectral step with a second spectral basis in the dictionary (Section 3,
+// step V with m_nu orthonormal bases; the Chebyshev basis of Section 4): the
+// dictionary is {DCT, B2} (DCT_ON) or {B2} alone.  S and Gamma_S stay in the
+// DCT domain, so basis 2's coefficients of a spectrum in that domain are
+// M (.) with M = C2 C^T (M[k2][k1]):
+//   V2 = S_{mu_nu/rho_V}(M S^ - Gamma_V2 / rho_V)                   (IV, old S)
+//   S^+ = ((Gamma_V + rho_V V) + M^T (Gamma_V2 + rho_V V2) - Gamma_S^ + rho_S X^)
+//         / (m_nu rho_V + rho_S)                                     (V)
+//   Gamma_V2 += rho_V (V2 - M S^+)                                   (VI, new S)
+// and the DCT terms as in k_spectral when DCT_ON.  Three more L x L products
+// per pixel spectrum (M S^, M^T Q2, M S^+), each staged through the shared tile.
+template <class R, int LP, int RESID, bool DCT_ON>
+__global__ void __launch_bounds__(SP_NT) k_spectral_b2(const R* __restrict__ X, R* __restrict__ GP, R* __restrict__ Sd,
+                                                        R* __restrict__ GV, R* __restrict__ GV2, R* __restrict__ GSd,
+                                                        R* __restrict__ b, const R* __restrict__ dctC,
+                                                        const R* __restrict__ Mb, int NN, int L, IterScalars<R> sc,
+                                                        double* __restrict__ partials) {
+  constexpr int PT = 4096 / LP;
+  constexpr int TP = PT / 4;
+  static_assert((LP / 4) * TP == SP_NT, "tile");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* C = reinterpret_cast<R*>(smem_raw);  // C[k][l]
+  R* CT = C + LP * LP;                     // CT[l][k]
+  R* M = CT + LP * LP;                     // M[k2][k1]
+  R* MT = M + LP * LP;                     // MT[k1][k2]
+  R* T = MT + LP * LP;                     // tile [LP][PT]
+  const int tid = threadIdx.x;
+  const int tk = tid / TP, tp = tid % TP;
+  const int p0 = blockIdx.x * PT;
+  for (int e = tid; e < LP * LP; e += SP_NT) {
+    const int k = e / LP, l = e % LP;
+    const R v = (k < L && l < L) ? dctC[k * L + l] : (R)0;
+    C[k * LP + l] = v;
+    CT[l * LP + k] = v;
+    const R m = (k < L && l < L) ? Mb[k * L + l] : (R)0;
+    M[k * LP + l] = m;
+    MT[l * LP + k] = m;
+  }
+  auto load_tile = [&](const R* src) {
+    for (int e = tid; e < LP * (PT / 4); e += SP_NT) {
+      const int l = e / (PT / 4), p = 4 * (e % (PT / 4));
+      R v[4] = {0, 0, 0, 0};
+      if (l < L && p0 + p < NN) V4<R>::ld(src + (size_t)l * NN + p0 + p, v);
+      V4<R>::st(T + l * PT + p, v);
+    }
+  };
+  // out[a][c] = sum_l A[kb + a][l] T[l][pb + c], with AT = A transposed in shared memory
+  auto product = [&](const R* AT, R (&out)[4][4], int kb, int pb) {
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int c = 0; c < 4; c++) out[a][c] = 0;
+#pragma unroll 4
+    for (int l = 0; l < LP; l++) {
+      R c4[4], x4[4];
+      V4<R>::ld(AT + l * LP + kb, c4);
+      V4<R>::ld(T + l * PT + pb, x4);
+#pragma unroll
+      for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) out[a][c] = fma(c4[a], x4[c], out[a][c]);
+    }
+  };
+  auto store_tile = [&](const R (&v)[4][4], int kb, int pb) {
+#pragma unroll
+    for (int a = 0; a < 4; a++) V4<R>::st(T + (kb + a) * PT + pb, v[a]);
+  };
+  load_tile(X);
+  __syncthreads();
+  const int kb = 4 * tk, pb = 4 * tp;
+  const bool pix_ok = p0 + pb < NN;
+  R xr[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; a++) V4<R>::ld(T + (kb + a) * PT + pb, xr[a]);
+  R xh[4][4];
+  product(CT, xh, kb, pb);  // X^ = C X
+  R r_dgv = 0, r_dgs = 0, r_l1 = 0, r_dgp = 0, r_x2 = 0, r_xmin = NoMin<R>::v;
+  bool r_bad = false;
+  if (RESID) {
+    // ||X W_2||_1 = sum |M X^| (and |X^| when the DCT is in the dictionary)
+    __syncthreads();
+    store_tile(xh, kb, pb);
+    __syncthreads();
+    R mx[4][4];
+    product(MT, mx, kb, pb);
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int c = 0; c < 4; c++)
+        if (kb + a < L && pix_ok) r_l1 += fabs(mx[a][c]) + (DCT_ON ? fabs(xh[a][c]) : (R)0);
+  }
+  // basis-2 coefficients of the old S
+  __syncthreads();
+  load_tile(Sd);
+  __syncthreads();
+  R v2[4][4], g2[4][4], q2[4][4];
+  {
+    R w2[4][4];
+    product(MT, w2, kb, pb);
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+      const int k = kb + a;
+      if (k < L && pix_ok) V4<R>::ld(GV2 + (size_t)k * NN + p0 + pb, g2[a]);
+      else for (int c = 0; c < 4; c++) g2[a][c] = 0;
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        v2[a][c] = soft_thr<R>(w2[a][c] - g2[a][c] * sc.inv_rho_V, sc.tau_V);
+        q2[a][c] = (k < L && pix_ok) ? g2[a][c] + sc.rho_V * v2[a][c] : (R)0;
+      }
+    }
+  }
+  __syncthreads();
+  store_tile(q2, kb, pb);
+  __syncthreads();
+  R z[4][4];
+  product(M, z, kb, pb);  // M^T Q2 in the DCT domain: sum_k2 M[k2][k1] Q2[k2]
+  // DCT-domain part of steps IV, V and VI
+  R u[4][4], sn_t[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    const int k = kb + a;
+#pragma unroll
+    for (int c = 0; c < 4; c++) u[a][c] = sn_t[a][c] = (R)0;
+    if (k < L && pix_ok) {
+      const size_t o = (size_t)k * NN + p0 + pb;
+      R s[4], gv[4], gs[4];
+      V4<R>::ld(Sd + o, s);
+      V4<R>::ld(GSd + o, gs);
+      if (DCT_ON) V4<R>::ld(GV + o, gv);
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        R q1 = 0, v1 = 0;
+        if (DCT_ON) {
+          v1 = soft_thr<R>(s[c] - gv[c] * sc.inv_rho_V, sc.tau_V);
+          q1 = gv[c] + sc.rho_V * v1;
+        }
+        const R sn = (q1 + z[a][c] - gs[c] + sc.rho_S * xh[a][c]) * sc.inv_VS;
+        const R gsn = gs[c] + sc.rho_S * (sn - xh[a][c]);
+        if (DCT_ON) {
+          const R gvn = gv[c] + sc.rho_V * (v1 - sn);
+          if (RESID) {
+            const R dv = gvn - gv[c];
+            r_dgv = fma(dv, dv, r_dgv);
+            r_bad |= !finite_<R>(gvn);
+          }
+          gv[c] = gvn;
+        }
+        if (RESID) {
+          const R ds = gsn - gs[c];
+          r_dgs = fma(ds, ds, r_dgs);
+          r_bad |= !finite_<R>(gsn);
+        }
+        s[c] = sn;
+        gs[c] = gsn;
+        sn_t[a][c] = sn;
+        u[a][c] = gsn + sc.rho_S * sn;
+      }
+      V4<R>::st(Sd + o, s);
+      V4<R>::st(GSd + o, gs);
+      if (DCT_ON) V4<R>::st(GV + o, gv);
+    }
+  }
+  // Gamma_V2 with the new S
+  __syncthreads();
+  store_tile(sn_t, kb, pb);
+  __syncthreads();
+  {
+    R m2[4][4];
+    product(MT, m2, kb, pb);
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+      const int k = kb + a;
+      if (k < L && pix_ok) {
+        R gn[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+          gn[c] = g2[a][c] + sc.rho_V * (v2[a][c] - m2[a][c]);
+          if (RESID) {
+            const R d = gn[c] - g2[a][c];
+            r_dgv = fma(d, d, r_dgv);
+            r_bad |= !finite_<R>(gn[c]);
+          }
+        }
+        V4<R>::st(GV2 + (size_t)k * NN + p0 + pb, gn);
+      }
+    }
+  }
+  __syncthreads();
+  store_tile(u, kb, pb);
+  __syncthreads();
+  R bs[4][4];
+  product(C, bs, kb, pb);  // (Gamma_S + rho_S S)[l] = sum_k C[k][l] U[k]
+  // pixel-domain part: step II, Gamma_P, and b
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    const int l = kb + a;
+    if (l < L && pix_ok) {
+      const size_t o = (size_t)l * NN + p0 + pb;
+      R gp[4], bo[4];
+      V4<R>::ld(GP + o, gp);
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        const R x = xr[a][c];
+        const R pt = x - gp[c] * sc.inv_rho_P;
+        const R pp = pt > (R)0 ? pt : (R)0;
+        const R gpn = gp[c] + sc.rho_P * (pp - x);
+        if (RESID) {
+          const R d = gpn - gp[c];
+          r_dgp = fma(d, d, r_dgp);
+          r_x2 = fma(x, x, r_x2);
+          r_xmin = x < r_xmin ? x : r_xmin;
+          r_bad |= !finite_<R>(x) || !finite_<R>(gpn);
+        }
+        gp[c] = gpn;
+        bo[c] = gpn + sc.rho_P * pp + bs[a][c];
+      }
+      V4<R>::st(GP + o, gp);
+      V4<R>::st(b + o, bo);
+    }
+  }
+  if (RESID) {
+    R q[Q_COUNT];
+#pragma unroll
+    for (int i = 0; i < Q_COUNT; i++) q[i] = 0;
+    q[Q_DGV] = r_dgv;
+    q[Q_DGS] = r_dgs;
+    q[Q_L1NU] = r_l1;
+    q[Q_DGP] = r_dgp;
+    q[Q_X2] = r_x2;
+    q[Q_XMIN] = r_xmin;
+    q[Q_NONFIN] = r_bad ? (R)1 : (R)0;
+    block_reduce_write<SP_NT>(q, partials + (size_t)blockIdx.x * MF_NQ);
+  }
+}
+
+template <class R, int LP, bool DCT_ON>
+static cudaError_t spectral_b2_lp(const R* X, R* GP, R* Sd, R* GV, R* GV2, R* GSd, R* b, const R* dctC, const R* Mb,
+                                  int N, int L, IterScalars<R> sc, double* partials, int resid, cudaStream_t s) {
+  constexpr int PT = 4096 / LP;
+  const int NN = N * N;
+  const int blocks = (NN + PT - 1) / PT;
+  const size_t sm = sizeof(R) * (4 * LP * LP + LP * PT);
+  cudaError_t e;
+  if (resid) {
+    e = cudaFuncSetAttribute(k_spectral_b2<R, LP, 1, DCT_ON>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_spectral_b2<R, LP, 1, DCT_ON><<<blocks, SP_NT, sm, s>>>(X, GP, Sd, GV, GV2, GSd, b, dctC, Mb, NN, L, sc,
+                                                               partials);
+  } else {
+    e = cudaFuncSetAttribute(k_spectral_b2<R, LP, 0, DCT_ON>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_spectral_b2<R, LP, 0, DCT_ON><<<blocks, SP_NT, sm, s>>>(X, GP, Sd, GV, GV2, GSd, b, dctC, Mb, NN, L, sc,
+                                                               partials);
+  }
+  return cudaGetLastError();
+}
+
+template <class R, bool DCT_ON>
+static cudaError_t spectral_b2_dispatch(const R* X, R* GP, R* Sd, R* GV, R* GV2, R* GSd, R* b, const R* dctC,
+                                        const R* Mb, int N, int L, IterScalars<R> sc, double* partials, int resid,
+                                        cudaStream_t s);
+
 // Adjoint of the spectral step (steps II, IV, V and their duals, and the
 // pointwise part of b) for the tied penalty rho, with the forward recomputed
 // from its inputs (X, old Gamma_P, S^, Gamma_V, Gamma_S^).  In: bb = cotangent
@@ -455,6 +717,33 @@ template cudaError_t launch_spectral<double>(const double*, double*, double*, do
                                              cudaStream_t);
 template int spectral_blocks<float>(int, int);
 template int spectral_blocks<double>(int, int);
+
+template <class R, bool DCT_ON>
+static cudaError_t spectral_b2_dispatch(const R* X, R* GP, R* Sd, R* GV, R* GV2, R* GSd, R* b, const R* dctC,
+                                        const R* Mb, int N, int L, IterScalars<R> sc, double* partials, int resid,
+                                        cudaStream_t s) {
+  switch (padded_L(L)) {
+    case 8: return spectral_b2_lp<R, 8, DCT_ON>(X, GP, Sd, GV, GV2, GSd, b, dctC, Mb, N, L, sc, partials, resid, s);
+    case 16: return spectral_b2_lp<R, 16, DCT_ON>(X, GP, Sd, GV, GV2, GSd, b, dctC, Mb, N, L, sc, partials, resid, s);
+    case 32: return spectral_b2_lp<R, 32, DCT_ON>(X, GP, Sd, GV, GV2, GSd, b, dctC, Mb, N, L, sc, partials, resid, s);
+    case 64: return spectral_b2_lp<R, 64, DCT_ON>(X, GP, Sd, GV, GV2, GSd, b, dctC, Mb, N, L, sc, partials, resid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class R>
+cudaError_t launch_spectral_b2(const R* X, R* GP, R* Sd, R* GV, R* GV2, R* GSd, R* b, const R* dctC, const R* Mb,
+                               int dct_on, int N, int L, IterScalars<R> sc, double* partials, int resid,
+                               cudaStream_t s) {
+  if (dct_on) return spectral_b2_dispatch<R, true>(X, GP, Sd, GV, GV2, GSd, b, dctC, Mb, N, L, sc, partials, resid, s);
+  return spectral_b2_dispatch<R, false>(X, GP, Sd, GV, GV2, GSd, b, dctC, Mb, N, L, sc, partials, resid, s);
+}
+template cudaError_t launch_spectral_b2<float>(const float*, float*, float*, float*, float*, float*, float*,
+                                               const float*, const float*, int, int, int, IterScalars<float>,
+                                               double*, int, cudaStream_t);
+template cudaError_t launch_spectral_b2<double>(const double*, double*, double*, double*, double*, double*, double*,
+                                                const double*, const double*, int, int, int, IterScalars<double>,
+                                                double*, int, cudaStream_t);
 
 // FP64 fold of the per-block partials into sums[MF_NQ]: a fixed thread count
 // and a fixed tree order, so the result does not depend on scheduling.
