@@ -71,6 +71,15 @@ def lib():
             L.orc_iterate_linear.argtypes = ([c_int, c_int, c_int, c_int, ip, dp, dp, dp, dp, dp, c_int, dp] +
                                              [dp] * 9 + [c_int, dp])
             L.orc_iterate_linear.restype = c_int
+            L.orc_vis_setup.argtypes = [c_int, c_int, ip, dp, dp, dp, dp, dp, dp]
+            L.orc_vis_setup.restype = c_int
+            L.orc_vis_apply.argtypes = [c_int, c_int, ip, dp, dp, dp, dp, dp, dp, c_int]
+            L.orc_vis_apply.restype = None
+            L.orc_solve_cg_vis.argtypes = [c_int, c_int, c_int, c_int, ip, dp, dp, ip, dp, dp, dp, c_int, dp, dp]
+            L.orc_solve_cg_vis.restype = c_int
+            L.orc_iterate_vis.argtypes = ([c_int, c_int, c_int, c_int, ip, dp, dp, ip, dp, dp, dp, dp, dp, c_int,
+                                           dp] + [dp] * 9 + [c_int, dp])
+            L.orc_iterate_vis.restype = c_int
             _lib = L
     return _lib
 
@@ -159,21 +168,7 @@ class Problem:
         self.y = np.ascontiguousarray(y, dtype=np.float64)
         self.L, self.N = self.y.shape[0], self.y.shape[-1]
         assert self.psf.shape == self.y.shape == (self.L, self.N, self.N)
-        self.J = J
-        self.bases = bases if bases is not None else daubechies.dictionary(mask)
-        self.nb = len(self.bases)
-        self.F = np.array([len(h) for _, h in self.bases], dtype=np.int32)
-        self.h = np.zeros((self.nb, MAXF))
-        for k, (_, h) in enumerate(self.bases):
-            self.h[k, : len(h)] = h
-        self.params = dict(params)
-        # spectral dictionary W_nu: a union of m_nu orthonormal bases (step V divides by m_nu rho_V + rho_S)
-        self.spectral = tuple(spectral)
-        self.mnu = len(self.spectral)
-        self.Cnu = [SPECTRAL_BASES[name](self.L) if isinstance(name, str) else np.asarray(name, dtype=np.float64)
-                    for name in self.spectral]
-        self.prm = np.concatenate([[float(self.params[k]) for k in PARAM_ORDER], [float(self.mnu)]] +
-                                  [C.ravel() for C in self.Cnu])
+        self._common(params, J, mask, bases, spectral)
         shp = (self.L, self.N, self.N)
         if conv not in ("circular", "linear"):
             raise ValueError(conv)
@@ -190,6 +185,59 @@ class Problem:
             rc = lib().orc_setup(self.N, self.L, _p(self.psf), _p(self.y), _p(self.hre), _p(self.him),
                                  _p(self.yre), _p(self.yim), _p(self.HtY))
         assert rc == 0
+
+    @classmethod
+    def visibilities(cls, N: int, uv, vis, params: dict, weights=None, J: int = 3, mask: int = 0x1FF, bases=None,
+                     cg_iters: int = 0, spectral=("dct",)):
+        """The problem of Section 2's last paragraph: y_l are the visibilities
+        vis[l] (complex [M_l]) sampled at uv[l] ([M_l, 2]: u, v in cells of the
+        N x N image's Fourier grid) with weights[l] (default 1), and H_l maps
+        the sky to them:
+          (Phi_l x)_m = sum_{r,c} x[r][c] exp(-2 pi i (u_m (c - N/2) + v_m (r - N/2)) / N);
+        the data fit is 1/2 sum_m w_m |y_m - (Phi_l x)_m|^2 and step I runs
+        cg_iters conjugate gradient iterations on Re(Phi_l^H W Phi_l) + rho I."""
+        self = cls.__new__(cls)
+        self.L, self.N = len(uv), int(N)
+        self._common(params, J, mask, bases, spectral)
+        self.conv, self.cg_iters = "vis", int(cg_iters)
+        counts = [len(np.asarray(a)) for a in uv]
+        assert [len(np.asarray(a)) for a in vis] == counts
+        self.voff = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+        UV = np.concatenate([np.asarray(a, dtype=np.float64).reshape(-1, 2) for a in uv])
+        self.u, self.v = np.ascontiguousarray(UV[:, 0]), np.ascontiguousarray(UV[:, 1])
+        if weights is None:
+            self.w = np.ones(len(self.u))
+        else:
+            self.w = np.ascontiguousarray(np.concatenate([np.asarray(a, dtype=np.float64) for a in weights]))
+        Y = np.concatenate([np.asarray(a, dtype=np.complex128) for a in vis])
+        self.y = Y
+        self.yre, self.yim = np.ascontiguousarray(Y.real), np.ascontiguousarray(Y.imag)
+        self.psf = None
+        self.HtY = np.empty((self.L, self.N, self.N))
+        rc = lib().orc_vis_setup(self.N, self.L, _ip(self.voff), _p(self.u), _p(self.v), _p(self.w), _p(self.yre),
+                                 _p(self.yim), _p(self.HtY))
+        assert rc == 0
+        return self
+
+    def _vis_args(self):
+        return (_ip(self.voff), _p(self.u), _p(self.v), _p(self.w))
+
+    def _common(self, params, J, mask, bases, spectral):
+        self.J = J
+        self.bases = bases if bases is not None else daubechies.dictionary(mask)
+        self.nb = len(self.bases)
+        self.F = np.array([len(h) for _, h in self.bases], dtype=np.int32)
+        self.h = np.zeros((self.nb, MAXF))
+        for k, (_, h) in enumerate(self.bases):
+            self.h[k, : len(h)] = h
+        self.params = dict(params)
+        # spectral dictionary W_nu: a union of m_nu orthonormal bases (step V divides by m_nu rho_V + rho_S)
+        self.spectral = tuple(spectral)
+        self.mnu = len(self.spectral)
+        self.Cnu = [SPECTRAL_BASES[name](self.L) if isinstance(name, str) else np.asarray(name, dtype=np.float64)
+                    for name in self.spectral]
+        self.prm = np.concatenate([[float(self.params[k]) for k in PARAM_ORDER], [float(self.mnu)]] +
+                                  [C.ravel() for C in self.Cnu])
 
     @property
     def rho_bar(self):
@@ -219,6 +267,9 @@ class Problem:
         if self.conv == "linear":
             rc = lib().orc_iterate_linear(*self._hdr(), _p(self.h2re), _p(self.h2im), _p(self.y), self.cg_iters,
                                           _p(self.HtY), *arrays, int(n_iter), hp)
+        elif self.conv == "vis":
+            rc = lib().orc_iterate_vis(*self._hdr(), *self._vis_args(), _p(self.yre), _p(self.yim), self.cg_iters,
+                                       _p(self.HtY), *arrays, int(n_iter), hp)
         else:
             rc = lib().orc_iterate(*self._hdr(), _p(self.hre), _p(self.him), _p(self.yre),
                                    _p(self.yim), _p(self.HtY), *arrays, int(n_iter), hp)
@@ -235,10 +286,13 @@ class Problem:
         Fourier filter (circular H), or cg_iters conjugate gradient iterations
         from x0 (default 0) for the linear H."""
         b = np.ascontiguousarray(b, dtype=np.float64)
-        if self.conv == "linear":
+        if self.conv in ("linear", "vis"):
             X = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64, order="C")
             it = self.cg_iters if cg_iters is None else int(cg_iters)
-            rc = lib().orc_solve_cg(*self._hdr(), _p(self.h2re), _p(self.h2im), it, _p(b), _p(X))
+            if self.conv == "vis":
+                rc = lib().orc_solve_cg_vis(*self._hdr(), *self._vis_args(), it, _p(b), _p(X))
+            else:
+                rc = lib().orc_solve_cg(*self._hdr(), _p(self.h2re), _p(self.h2im), it, _p(b), _p(X))
         else:
             X = np.empty_like(b)
             rc = lib().orc_solve(*self._hdr(), _p(self.hre), _p(self.him), _p(b), _p(X))
@@ -246,7 +300,21 @@ class Problem:
         return X
 
     def apply_H(self, x: np.ndarray, adjoint: bool = False) -> np.ndarray:
-        """H x (or H^T x) of the linear convolution, for every band."""
+        """H x (or H^T x) of the linear convolution, for every band.  For the
+        visibility operator: Phi x (x a real cube; returns the concatenated
+        complex visibilities) or, adjoint, Re(Phi^H W x) (x complex visibilities)."""
+        if self.conv == "vis":
+            n = int(self.voff[-1])
+            if adjoint:
+                z = np.asarray(x, dtype=np.complex128)
+                zre, zim = np.ascontiguousarray(z.real), np.ascontiguousarray(z.imag)
+                out = np.empty((self.L, self.N, self.N))
+                lib().orc_vis_apply(self.N, self.L, *self._vis_args(), _p(out), _p(zre), _p(zim), 1)
+                return out
+            xc = np.ascontiguousarray(x, dtype=np.float64)
+            zre, zim = np.empty(n), np.empty(n)
+            lib().orc_vis_apply(self.N, self.L, *self._vis_args(), _p(xc), _p(zre), _p(zim), 0)
+            return zre + 1j * zim
         assert self.conv == "linear"
         x = np.ascontiguousarray(x, dtype=np.float64)
         out = np.empty_like(x)

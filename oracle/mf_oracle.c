@@ -34,6 +34,10 @@
  *   - W_nu is the orthonormal DCT-II along the band axis, so m_nu = 1:
  *     (X W_nu)[k] = sum_l C[k][l] X[l] with C[k][l] = a_k cos(pi (2l+1) k / (2L)).
  *   - S_r(0) = 0.
+ *   - Two other forms of H_l, each with step I by conjugate gradients (the
+ *     solver Algorithm 1's comment names): the linear ("same"-size)
+ *     convolution by the PSF, and the operator from the sky to sampled
+ *     visibilities of Section 2's last paragraph (both described below).
  *
  * Layout: every cube is [L][N][N] row-major; the wavelet-domain arrays T and
  * Gamma_T are [nb][L][N][N] (basis-major), each band in the in-place layout above.
@@ -384,11 +388,31 @@ static void solve_x(const problem* pb, const double* hre, const double* him,
  * (u - N/2) mod 2N, the circular convolution of size 2N has no wrap-around on
  * the cropped [0,N)^2 output.
  */
+/*
+ * Visibility-domain operator (Section 2, last paragraph: y_l are the sampled
+ * visibilities and H_l maps the sky to them).  Reading: band l has the
+ * visibilities m in [voff[l], voff[l+1]) at uv coordinates (u_m, v_m), in
+ * cells of the N x N image's Fourier grid, with weights w_m >= 0, and
+ *   (Phi_l x)_m = sum_{r,c} x[r][c] exp(-2 pi i (u_m (c - N/2) + v_m (r - N/2)) / N)
+ * (phase centre at pixel (N/2, N/2), column index along u).  The data-fit term
+ * is 1/2 sum_m w_m |y_m - (Phi_l x)_m|^2 and, x being real, step I's matrix is
+ * Q_l = Re(Phi_l^H W Phi_l) + rho I with right-hand side Re(Phi_l^H W y_l) + b_l.
+ */
+typedef struct {
+  const int* voff;     /* [L+1] */
+  const double* u;     /* [voff[L]] uv coordinates, cells */
+  const double* v;
+  const double* w;     /* weights */
+  const double* yre;   /* visibilities */
+  const double* yim;
+} vis_data;
+
 typedef struct {
   const double* h2re;  /* [L][2N][2N] transfer function of the embedded PSF */
   const double* h2im;
   const double* y;     /* dirty cube [L][N][N], for the data-fit term */
   int cg_iters;
+  const vis_data* vis; /* not NULL: H_l is the visibility operator instead */
 } lin_op;
 
 /* out = H x (adjoint = 0) or H^T x (adjoint = 1) for one band; buffers re, im hold (2N)^2 each. */
@@ -456,6 +480,92 @@ void orc_linear_apply(int N, int L, const double* h2re, const double* h2im, cons
   free(twr); free(twi);
 }
 
+/* e^{-2 pi i f (n - N/2) / N} for n in [0, N): the phases of one uv coordinate f along a pixel axis */
+static void vis_phases(int N, double f, double* cr, double* ci) {
+  for (int n = 0; n < N; n++) {
+    double a = -2.0 * M_PI * f * (double)(n - N / 2) / (double)N;
+    cr[n] = cos(a);
+    ci[n] = sin(a);
+  }
+}
+
+/* t = Phi_l x for band l (t indexed from the band's first visibility); buf holds 4N doubles */
+static void vis_forward_band(int N, const vis_data* vd, int l, const double* x, double* tre, double* tim,
+                             double* buf) {
+  double *exr = buf, *exi = buf + N, *eyr = buf + 2 * N, *eyi = buf + 3 * N;
+  for (int m = vd->voff[l]; m < vd->voff[l + 1]; m++) {
+    vis_phases(N, vd->u[m], exr, exi);
+    vis_phases(N, vd->v[m], eyr, eyi);
+    double sr = 0.0, si = 0.0;
+    for (int r = 0; r < N; r++) {
+      double ar = 0.0, ai = 0.0; /* sum over the row of x[r][c] e_u[c] */
+      for (int c = 0; c < N; c++) {
+        ar += x[(long)r * N + c] * exr[c];
+        ai += x[(long)r * N + c] * exi[c];
+      }
+      sr += ar * eyr[r] - ai * eyi[r];
+      si += ar * eyi[r] + ai * eyr[r];
+    }
+    tre[m - vd->voff[l]] = sr;
+    tim[m - vd->voff[l]] = si;
+  }
+}
+
+/* out = Re(Phi_l^H W z) for band l (z indexed from the band's first visibility) */
+static void vis_adjoint_band(int N, const vis_data* vd, int l, const double* zre, const double* zim, double* out,
+                             double* buf) {
+  double *exr = buf, *exi = buf + N, *eyr = buf + 2 * N, *eyi = buf + 3 * N;
+  for (long i = 0; i < (long)N * N; i++) out[i] = 0.0;
+  for (int m = vd->voff[l]; m < vd->voff[l + 1]; m++) {
+    vis_phases(N, vd->u[m], exr, exi);
+    vis_phases(N, vd->v[m], eyr, eyi);
+    double wt = vd->w ? vd->w[m] : 1.0;
+    double cr = wt * zre[m - vd->voff[l]], ci = wt * zim[m - vd->voff[l]];
+    for (int r = 0; r < N; r++) {
+      /* a + ib = w z conj(e_v[r]); out[r][c] += Re((a + ib) conj(e_u[c])) */
+      double a = cr * eyr[r] + ci * eyi[r];
+      double b = ci * eyr[r] - cr * eyi[r];
+      for (int c = 0; c < N; c++) out[(long)r * N + c] += a * exr[c] + b * exi[c];
+    }
+  }
+}
+
+static int vis_max_count(const vis_data* vd, int L) {
+  int mx = 1;
+  for (int l = 0; l < L; l++)
+    if (vd->voff[l + 1] - vd->voff[l] > mx) mx = vd->voff[l + 1] - vd->voff[l];
+  return mx;
+}
+
+/* HtY = Re(Phi^H W y) for every band. */
+int orc_vis_setup(int N, int L, const int* voff, const double* u, const double* v, const double* w,
+                  const double* yre, const double* yim, double* HtY) {
+  vis_data vd = {voff, u, v, w, yre, yim};
+  for (int l = 0; l < L; l++)
+    if (voff[l + 1] < voff[l]) return 1;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int l = 0; l < L; l++) {
+    double* buf = malloc(sizeof(double) * 4 * N);
+    vis_adjoint_band(N, &vd, l, yre + voff[l], yim + voff[l], HtY + (long)l * N * N, buf);
+    free(buf);
+  }
+  return 0;
+}
+
+/* Phi x (adjoint 0: x real [L][N][N] -> (zre, zim) [voff[L]]) or Re(Phi^H W z) (adjoint 1: z -> x). */
+void orc_vis_apply(int N, int L, const int* voff, const double* u, const double* v, const double* w, double* x,
+                   double* zre, double* zim, int adjoint) {
+  vis_data vd = {voff, u, v, w, NULL, NULL};
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int l = 0; l < L; l++) {
+    double* buf = malloc(sizeof(double) * 4 * N);
+    double* xl = x + (long)l * N * N;
+    if (adjoint) vis_adjoint_band(N, &vd, l, zre + voff[l], zim + voff[l], xl, buf);
+    else vis_forward_band(N, &vd, l, xl, zre + voff[l], zim + voff[l], buf);
+    free(buf);
+  }
+}
+
 static double dot(const double* a, const double* b, long n) {
   double s = 0.0;
   for (long i = 0; i < n; i++) s += a[i] * b[i];
@@ -470,34 +580,94 @@ static double dot(const double* a, const double* b, long n) {
  * A zero residual or a zero p.q ends the band's iterations (the system is solved).
  * If dfit is not NULL it receives per band 1/2 ||y_l - H_l x_l||^2 for the final x.
  */
+/* Per-band work buffers of the normal operator H_l^T H_l (or Re(Phi_l^H W Phi_l)). */
+typedef struct {
+  double *re, *im, *lr, *li, *t; /* linear convolution: (2N)^2 FFT image, FFT line, H x */
+  double *zr, *zi, *buf;         /* visibilities: Phi x, phase tables */
+} normal_ws;
+
+static void normal_ws_alloc(normal_ws* ws, int N, const lin_op* lo, int L) {
+  long M = 2L * N, NN = (long)N * N;
+  memset(ws, 0, sizeof(*ws));
+  if (lo->vis) {
+    int mx = vis_max_count(lo->vis, L);
+    ws->zr = malloc(sizeof(double) * mx);
+    ws->zi = malloc(sizeof(double) * mx);
+    ws->buf = malloc(sizeof(double) * 4 * N);
+  } else {
+    ws->re = malloc(sizeof(double) * M * M);
+    ws->im = malloc(sizeof(double) * M * M);
+    ws->lr = malloc(sizeof(double) * M);
+    ws->li = malloc(sizeof(double) * M);
+    ws->t = malloc(sizeof(double) * NN);
+  }
+}
+
+static void normal_ws_free(normal_ws* ws) {
+  free(ws->re); free(ws->im); free(ws->lr); free(ws->li); free(ws->t);
+  free(ws->zr); free(ws->zi); free(ws->buf);
+}
+
+/* q = H_l^T H_l x for band l */
+static void normal_band(int N, const lin_op* lo, int l, const double* x, double* q, normal_ws* ws,
+                        const double* twr, const double* twi) {
+  if (lo->vis) {
+    vis_forward_band(N, lo->vis, l, x, ws->zr, ws->zi, ws->buf);
+    vis_adjoint_band(N, lo->vis, l, ws->zr, ws->zi, q, ws->buf);
+  } else {
+    long MM = 4L * N * N;
+    const double* hr = lo->h2re + l * MM;
+    const double* hi = lo->h2im + l * MM;
+    lin_apply_band(N, hr, hi, x, ws->t, 0, ws->re, ws->im, twr, twi, ws->lr, ws->li);
+    lin_apply_band(N, hr, hi, ws->t, q, 1, ws->re, ws->im, twr, twi, ws->lr, ws->li);
+  }
+}
+
+/* 1/2 ||y_l - H_l x||^2 (linear convolution) or 1/2 sum_m w_m |y_m - (Phi_l x)_m|^2 */
+static double data_fit_band(int N, const lin_op* lo, int l, const double* x, normal_ws* ws, const double* twr,
+                            const double* twi) {
+  double f = 0.0;
+  if (lo->vis) {
+    const vis_data* vd = lo->vis;
+    vis_forward_band(N, vd, l, x, ws->zr, ws->zi, ws->buf);
+    for (int m = vd->voff[l]; m < vd->voff[l + 1]; m++) {
+      double dr = vd->yre[m] - ws->zr[m - vd->voff[l]], di = vd->yim[m] - ws->zi[m - vd->voff[l]];
+      f += (vd->w ? vd->w[m] : 1.0) * (dr * dr + di * di);
+    }
+  } else {
+    long NN = (long)N * N, MM = 4L * N * N;
+    lin_apply_band(N, lo->h2re + l * MM, lo->h2im + l * MM, x, ws->t, 0, ws->re, ws->im, twr, twi, ws->lr, ws->li);
+    for (long i = 0; i < NN; i++) {
+      double d = lo->y[l * NN + i] - ws->t[i];
+      f += d * d;
+    }
+  }
+  return 0.5 * f;
+}
+
 static void solve_cg(const problem* pb, const lin_op* lo, const double* b, double* X, double* dfit) {
   int N = pb->N, L = pb->L, M = 2 * N;
-  long NN = (long)N * N, MM = (long)M * M;
+  long NN = (long)N * N;
   double rho = pb->mu_eps + pb->rho_S + pb->rho_P + pb->nb * pb->rho_T; /* Eq. Qlsimp */
   double* twr = malloc(sizeof(double) * (M / 2 + 1));
   double* twi = malloc(sizeof(double) * (M / 2 + 1));
   twiddles(M, twr, twi);
 #pragma omp parallel for schedule(dynamic, 1)
   for (int l = 0; l < L; l++) {
-    const double* hr = lo->h2re + l * MM;
-    const double* hi = lo->h2im + l * MM;
-    double *re = malloc(sizeof(double) * MM), *im = malloc(sizeof(double) * MM);
-    double *lr = malloc(sizeof(double) * M), *li = malloc(sizeof(double) * M);
+    normal_ws ws;
+    normal_ws_alloc(&ws, N, lo, L);
     double *r = malloc(sizeof(double) * NN), *p = malloc(sizeof(double) * NN), *q = malloc(sizeof(double) * NN);
-    double* t = malloc(sizeof(double) * NN);
     double* x = X + l * NN;
     const double* bl = b + l * NN;
     /* r = b - Q x */
-    lin_apply_band(N, hr, hi, x, t, 0, re, im, twr, twi, lr, li);
-    lin_apply_band(N, hr, hi, t, q, 1, re, im, twr, twi, lr, li);
+    normal_band(N, lo, l, x, q, &ws, twr, twi);
     for (long i = 0; i < NN; i++) {
       r[i] = bl[i] - (q[i] + rho * x[i]);
       p[i] = r[i];
     }
     double g = dot(r, r, NN);
     for (int it = 0; it < lo->cg_iters && g > 0.0; it++) {
-      lin_apply_band(N, hr, hi, p, t, 0, re, im, twr, twi, lr, li);
-      lin_apply_band(N, hr, hi, t, q, 1, re, im, twr, twi, lr, li);
+      normal_band(N, lo, l, p, q, &ws, twr, twi);
       for (long i = 0; i < NN; i++) q[i] += rho * p[i];
       double pq = dot(p, q, NN);
       if (!(pq > 0.0)) break;
@@ -511,16 +681,9 @@ static void solve_cg(const problem* pb, const lin_op* lo, const double* b, doubl
       for (long i = 0; i < NN; i++) p[i] = r[i] + beta * p[i];
       g = g2;
     }
-    if (dfit) {
-      lin_apply_band(N, hr, hi, x, t, 0, re, im, twr, twi, lr, li);
-      double f = 0.0;
-      for (long i = 0; i < NN; i++) {
-        double d = lo->y[l * NN + i] - t[i];
-        f += d * d;
-      }
-      dfit[l] = 0.5 * f;
-    }
-    free(re); free(im); free(lr); free(li); free(r); free(p); free(q); free(t);
+    if (dfit) dfit[l] = data_fit_band(N, lo, l, x, &ws, twr, twi);
+    normal_ws_free(&ws);
+    free(r); free(p); free(q);
   }
   free(twr); free(twi);
 }
@@ -530,7 +693,18 @@ int orc_solve_cg(int N, int L, int J, int nb, const int* F, const double* h, con
                  const double* h2im, int cg_iters, const double* b, double* X) {
   problem pb;
   if (load_problem(&pb, N, L, J, nb, F, h, prm)) return 1;
-  lin_op lo = {h2re, h2im, NULL, cg_iters};
+  lin_op lo = {h2re, h2im, NULL, cg_iters, NULL};
+  solve_cg(&pb, &lo, b, X, NULL);
+  return 0;
+}
+
+/* Step I alone with CG for the visibility operator (see vis_data). */
+int orc_solve_cg_vis(int N, int L, int J, int nb, const int* F, const double* h, const double* prm, const int* voff,
+                     const double* u, const double* v, const double* w, int cg_iters, const double* b, double* X) {
+  problem pb;
+  if (load_problem(&pb, N, L, J, nb, F, h, prm)) return 1;
+  vis_data vd = {voff, u, v, w, NULL, NULL};
+  lin_op lo = {NULL, NULL, NULL, cg_iters, &vd};
   solve_cg(&pb, &lo, b, X, NULL);
   return 0;
 }
@@ -792,7 +966,20 @@ int orc_iterate_linear(int N, int L, int J, int nb, const int* F, const double* 
                        const double* h2re, const double* h2im, const double* y, int cg_iters, const double* HtY,
                        double* X, double* P, double* T, double* V, double* S, double* GP, double* GT, double* GV,
                        double* GS, int n_iter, double* hist) {
-  lin_op lo = {h2re, h2im, y, cg_iters};
+  lin_op lo = {h2re, h2im, y, cg_iters, NULL};
+  return iterate_impl(N, L, J, nb, F, h, prm, NULL, NULL, NULL, NULL, &lo, HtY, X, P, T, V, S, GP, GT, GV, GS, n_iter,
+                      hist);
+}
+
+/* Algorithm 1 with the visibility operator (see vis_data): step I by cg_iters conjugate
+ * gradient iterations per band from the previous X, HtY = Re(Phi^H W y) (orc_vis_setup);
+ * the history's data-fit term is formed in the visibility domain. */
+int orc_iterate_vis(int N, int L, int J, int nb, const int* F, const double* h, const double* prm, const int* voff,
+                    const double* u, const double* v, const double* w, const double* yre, const double* yim,
+                    int cg_iters, const double* HtY, double* X, double* P, double* T, double* V, double* S,
+                    double* GP, double* GT, double* GV, double* GS, int n_iter, double* hist) {
+  vis_data vd = {voff, u, v, w, yre, yim};
+  lin_op lo = {NULL, NULL, NULL, cg_iters, &vd};
   return iterate_impl(N, L, J, nb, F, h, prm, NULL, NULL, NULL, NULL, &lo, HtY, X, P, T, V, S, GP, GT, GV, GS, n_iter,
                       hist);
 }

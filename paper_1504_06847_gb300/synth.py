@@ -25,6 +25,16 @@ Recipe (all draws from ``numpy.random.default_rng(seed)`` in this order):
    shifted so that the peak sits at pixel (N/2, N/2);
 4. ``y_l = psf_l (circularly convolved) x_l + n``, ``n ~ N(0, sigma^2)`` with
    ``sigma = rms(Hx) * 10^(-snr_db/20)``.
+
+Visibility-domain observations (``make_visibilities``, the measurement model of
+Section 2's last paragraph): the same sky and array draws, then per band one
+visibility per unordered baseline i < j at the continuous uv point
+``(p_i - p_j) * (nu_l/nu_0) * N/10`` (cells; rounded to float32 so that every
+consumer sees the same coordinates), the exact sum
+``sum_{r,c} x[r][c] exp(-2 pi i (u (c - N/2) + v (r - N/2)) / N)`` plus complex
+white noise (each part of standard deviation ``sigma/sqrt(2)``,
+``sigma = rms|Phi x| * 10^(-snr_db/20)``), and weights 1 or, with
+``random_weights``, ``U(0.5, 1.5)``.
 """
 
 from __future__ import annotations
@@ -63,6 +73,56 @@ def make_cube(N: int, L: int, n_sources: int, n_antennas: int, seed: int,
     rng = np.random.default_rng(seed)
     nu = 1.0 + np.arange(L) / (L - 1)
     nu0 = 1.0
+    sky = _sky(N, L, n_sources, rng, nu, nu0, point_frac)
+    return observe(sky, nu, nu0, n_antennas, rng, snr_db)
+
+
+@dataclasses.dataclass
+class Visibilities:
+    sky: np.ndarray  # [L][N][N] float64, the synthetic truth (>= 0)
+    uv: list  # L arrays [M_l, 2] float64 (float32-representable), (u, v) in cells
+    vis: list  # L arrays [M_l] complex128
+    weights: list  # L arrays [M_l] float64
+    nu: np.ndarray  # [L] GHz
+    sigma: float  # noise standard deviation (complex)
+
+
+def make_visibilities(N: int, L: int, n_sources: int, n_antennas: int, seed: int, snr_db: float = 20.0,
+                      random_weights: bool = False, point_frac: float = 0.0) -> Visibilities:
+    """The recipe's sky and array, observed as visibilities (see the module docstring)."""
+    if L < 2:
+        raise ValueError("L must be >= 2")
+    rng = np.random.default_rng(seed)
+    nu = 1.0 + np.arange(L) / (L - 1)
+    nu0 = 1.0
+    sky = _sky(N, L, n_sources, rng, nu, nu0, point_frac)
+    r = np.sqrt(rng.uniform(0.0, 1.0, size=n_antennas))
+    th = rng.uniform(0.0, 2.0 * np.pi, size=n_antennas)
+    pos = np.stack([r * np.cos(th), r * np.sin(th)], axis=1)
+    i, j = np.triu_indices(n_antennas, k=1)
+    base = pos[i] - pos[j]
+    uvs, clean = [], []
+    n = np.arange(N) - N // 2
+    for l in range(L):
+        uv = (base * (nu[l] / nu0) * N / 10.0).astype(np.float32).astype(np.float64)
+        eu = np.exp(-2j * np.pi * np.outer(uv[:, 0], n) / N)  # [M, N] along columns
+        ev = np.exp(-2j * np.pi * np.outer(uv[:, 1], n) / N)  # [M, N] along rows
+        clean.append(np.einsum("mr,mr->m", ev, eu @ sky[l].T))
+        uvs.append(uv)
+    allv = np.concatenate(clean)
+    sigma = float(np.sqrt(np.mean(np.abs(allv) ** 2)) * 10.0 ** (-snr_db / 20.0))
+    vis = [v + rng.normal(0.0, sigma / np.sqrt(2), size=v.shape) + 1j * rng.normal(0.0, sigma / np.sqrt(2),
+                                                                                     size=v.shape)
+           for v in clean]
+    if random_weights:
+        weights = [rng.uniform(0.5, 1.5, size=len(v)) for v in vis]
+    else:
+        weights = [np.ones(len(v)) for v in vis]
+    return Visibilities(sky=sky, uv=uvs, vis=vis, weights=weights, nu=nu, sigma=sigma)
+
+
+def _sky(N, L, n_sources, rng, nu, nu0, point_frac):
+    """Step 2 of the recipe: the sky cube [L][N][N]."""
     lognu = np.log(nu / nu0)
 
     sky = np.zeros((L, N, N))
@@ -85,8 +145,7 @@ def make_cube(N: int, L: int, n_sources: int, n_antennas: int, seed: int,
                 img = np.zeros((N, N))
                 np.add.at(img, (ry[:, None], rx[None, :]), g)
                 sky += spec[:, None, None] * img[None]
-
-    return observe(sky, nu, nu0, n_antennas, rng, snr_db)
+    return sky
 
 
 def observe(sky: np.ndarray, nu: np.ndarray, nu0: float, n_antennas: int, rng, snr_db: float = 20.0) -> Cube:
