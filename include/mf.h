@@ -121,12 +121,38 @@ mf_status mf_plan_create_f64(int N, int L, const double* psf_cube, mf_plan** out
  * circular plan (transfer function and work arrays at 2N, the CG vectors).
  * mf_admm_backward rejects it.  Errors: MF_ERR_INVALID, MF_ERR_OOM, MF_ERR_CUDA. */
 mf_status mf_plan_create_linear(int N, int L, const float* psf_cube, mf_plan** out);
+
+/* An FP32 plan for the visibility-domain form of the model (Section 2, last
+ * paragraph): y_l are the complex visibilities of band l and H_l maps the sky
+ * to them,
+ *   (Phi_l x)_m = sum_{r,c} x[r][c] exp(-2 pi i (u_m (c - N/2) + v_m (r - N/2)) / N),
+ * with the data-fit term 1/2 sum_m w_m |y_m - (Phi_l x)_m|^2.  x being real,
+ * Q_l = Re(Phi_l^H W Phi_l) + rho I (Eq. Qlsimp with H_l = Phi_l) and the
+ * right-hand side of Eq. matB has Re(Phi_l^H W y_l) for H^T y.  Step I runs
+ * prm->cg_iters conjugate gradient iterations per band from the previous X
+ * (as for mf_plan_create_linear); Re(Phi^H W Phi) is applied as the Toeplitz
+ * convolution it is (one 2N x 2N FFT round trip), whose kernel the plan
+ * computes here by gridding (a type-1 non-uniform FFT, exponential-of-
+ * semicircle kernel, width 8, oversampling 2); the dirty image Re(Phi^H W y)
+ * is computed the same way at the start of every mf_admm_iterate call.
+ *   n_vis   : host [L], visibilities per band (>= 0)
+ *   uv      : device float [sum n_vis][2], (u_m, v_m) in cells of the N x N
+ *             image's Fourier grid, band after band; |u|, |v| < N/2
+ *   weights : device float [sum n_vis], w_m >= 0, or NULL (all 1)
+ * Both are copied (the caller keeps its buffers).  mf_admm_iterate on this plan
+ * takes y_cube = device float [sum n_vis][2], the complex visibilities
+ * (re, im), in the same order.  N is a power of two in [16, 512].
+ * mf_admm_backward rejects it.  Errors: MF_ERR_INVALID (sizes, NULL, a uv
+ * point or weight out of range or not finite), MF_ERR_OOM, MF_ERR_CUDA. */
+mf_status mf_plan_create_vis(int N, int L, const int* n_vis, const float* uv, const float* weights,
+                             mf_plan** out);
 /* Frees everything the plan owns; NULL is a no-op.  Synchronises the device. */
 void mf_plan_destroy(mf_plan* p);
 size_t mf_plan_device_bytes(const mf_plan* p);
 
 /* Runs n_iter >= 1 iterations of Algorithm 1 on the dirty cube y_cube
- * (device [L][N][N] float, read during the enqueued work).  Constants
+ * (device [L][N][N] float, read during the enqueued work; for a plan from
+ * mf_plan_create_vis, the visibilities described there).  Constants
  * H^T y and the Fourier filter are recomputed on every call.  Returns
  * MF_ERR_INVALID for bad parameters (rho <= 0, mu < 0, J, mask, precision
  * not matching the plan), otherwise the plan's latched status. */
@@ -173,7 +199,9 @@ typedef enum {
   MF_ARR_GAMMA_T = 6,  /* Gamma_T: [nd][L][N][N], nd distinct bases in mask order
                           (Db1..Db8, Haar folded into Db1 when both are on),
                           each band in the in-place Mallat layout */
-  MF_ARR_GAMMA_V2 = 7  /* Gamma_V of the Chebyshev spectral basis (its coefficient domain) */
+  MF_ARR_GAMMA_V2 = 7, /* Gamma_V of the Chebyshev spectral basis (its coefficient domain) */
+  MF_ARR_HTY = 8       /* plans from mf_plan_create_linear / _vis: H^T y of the last call
+                          (Re(Phi^H W y) for visibilities); get only */
 } mf_array;
 
 /* Device-to-device copies of a state array (dst/src: device, plan's real

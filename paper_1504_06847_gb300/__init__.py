@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libmf.so")
 MF_OK, MF_ERR_INVALID, MF_ERR_OOM, MF_ERR_CUDA, MF_ERR_TIMEOUT, MF_ERR_NONFINITE, MF_ERR_TOO_LARGE = range(7)
 XSTEP_NOALLOC_MAX_VOXELS = 1 << 19
 MF_FP32, MF_FP64, MF_FP32_DCT_SPLITBF16 = range(3)
-ARR_X, ARR_GAMMA_P, ARR_S_DCT, ARR_GAMMA_V, ARR_GAMMA_S_DCT, ARR_B, ARR_GAMMA_T, ARR_GAMMA_V2 = range(8)
+ARR_X, ARR_GAMMA_P, ARR_S_DCT, ARR_GAMMA_V, ARR_GAMMA_S_DCT, ARR_B, ARR_GAMMA_T, ARR_GAMMA_V2, ARR_HTY = range(9)
 SPECTRAL_DCT, SPECTRAL_CHEBYSHEV = 0, 1
 
 EXPORTS = ["mf_params_default", "mf_plan_create", "mf_plan_create_f64", "mf_plan_destroy",
@@ -26,7 +26,7 @@ EXPORTS = ["mf_params_default", "mf_plan_create", "mf_plan_create_f64", "mf_plan
            "mf_wavelet_filter", "mf_status_string", "mf_plan_set_timing", "mf_plan_get_timing",
            "mf_kernel_name", "mf_xstep_noalloc", "mf_plan_set_option", "mf_batch_iterate",
            "mf_admm_backward", "mf_plan_clear_status", "mf_spectral_index", "mf_plan_create_linear",
-           "mf_spectral_basis"]
+           "mf_spectral_basis", "mf_plan_create_vis"]
 MF_OPT_WAV_TILE, MF_OPT_TEST_TC_STALL = 0, 1
 
 KERNELS = ["rows_fwd", "cols_solve", "rows_inv", "spectral", "wav_ll", "wav_level1", "wav_levelj", "setup",
@@ -76,6 +76,9 @@ def lib():
             f = getattr(L, name)
             f.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(vp)]
             f.restype = ctypes.c_int
+        L.mf_plan_create_vis.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp, vp,
+                                         ctypes.POINTER(vp)]
+        L.mf_plan_create_vis.restype = ctypes.c_int
         L.mf_plan_destroy.argtypes = [vp]
         L.mf_plan_destroy.restype = None
         L.mf_plan_device_bytes.argtypes = [vp]
@@ -239,7 +242,40 @@ class Plan:
     psf: CUDA tensor [L, N, N] (float32, or float64 for an FP64 plan).
     linear=True: H is the linear (zero-padded, non-circulant) convolution and
     step I runs conjugate gradients (float32; see mf_plan_create_linear).
+    Plan.from_visibilities: H maps the sky to sampled visibilities (see
+    mf_plan_create_vis); iterate() then takes the visibilities.
     """
+
+    n_vis = None
+
+    @classmethod
+    def from_visibilities(cls, N: int, uv, weights=None):
+        """uv: list of L CUDA float32 tensors [M_l, 2] ((u, v) in cells of the
+        N x N image's Fourier grid); weights: list of L CUDA float32 tensors
+        [M_l] or None (all 1).  The plan copies both."""
+        import torch
+
+        self = cls.__new__(cls)
+        self.L, self.N = len(uv), int(N)
+        self.dtype = torch.float32
+        self.device = uv[0].device
+        counts = [int(a.shape[0]) for a in uv]
+        self.n_vis = sum(counts)
+        cat = torch.cat([a.reshape(-1, 2) for a in uv]).to(torch.float32).contiguous()
+        if not cat.is_cuda:
+            raise ValueError("uv must be CUDA tensors")
+        wc = None
+        if weights is not None:
+            wc = torch.cat([a.reshape(-1) for a in weights]).to(torch.float32).contiguous()
+            if wc.shape[0] != self.n_vis or not wc.is_cuda:
+                raise ValueError("weights must match uv")
+        c_counts = (ctypes.c_int * self.L)(*counts)
+        h = ctypes.c_void_p()
+        _check(lib().mf_plan_create_vis(self.N, self.L, c_counts, ctypes.c_void_p(cat.data_ptr()),
+                                        ctypes.c_void_p(wc.data_ptr()) if wc is not None else None,
+                                        ctypes.byref(h)), "mf_plan_create_vis")
+        self._h = h
+        return self
 
     def __init__(self, psf, linear: bool = False):
         import torch
@@ -290,7 +326,13 @@ class Plan:
 
         if params is None:
             params = self.params(**kw)
-        if y.dtype != self.dtype or not y.is_cuda or tuple(y.shape) != (self.L, self.N, self.N):
+        if self.n_vis is not None:
+            # visibilities: complex64 [sum M_l] (or float32 [sum M_l, 2])
+            if y.dtype == torch.complex64:
+                y = torch.view_as_real(y.contiguous())
+            if y.dtype != torch.float32 or not y.is_cuda or tuple(y.shape) != (self.n_vis, 2):
+                raise ValueError("y must be the plan's visibilities: CUDA complex64 [sum M_l]")
+        elif y.dtype != self.dtype or not y.is_cuda or tuple(y.shape) != (self.L, self.N, self.N):
             raise ValueError("y must be a CUDA tensor [L, N, N] of the plan's dtype")
         y = y.contiguous()
         f = lib().mf_admm_iterate if self.dtype == torch.float32 else lib().mf_admm_iterate_f64

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmf.so")
 SOURCES = ["plan.cu", "fft.cu", "spectral.cu", "spectral_tc.cu", "wavelet.cu", "noalloc.cu", "backward.cu", "dual.cu",
-           "spindex.cu", "cg.cu",
+           "spindex.cu", "cg.cu", "vis.cu",
            "daub.cpp", "chebyshev.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")

@@ -228,12 +228,14 @@ cudaError_t conv2n(mf_plan* p, int mode, cudaStream_t s) {
   return e;
 }
 
-// big <- H^T crop(H pad(src)) (2N x 2N; the caller reads its [0,N)^2 region)
+// big <- H^T crop(H pad(src)) (2N x 2N; the caller reads its [0,N)^2 region).
+// Visibility plans: big <- kr * pad(src), the Toeplitz form of Re(Phi^H W Phi) (vis.cu).
 cudaError_t apply_hth(mf_plan* p, const float* src, cudaStream_t s) {
   const size_t big_n = (size_t)4 * p->cube;
   k_pad<<<grid_of(big_n), CNT, 0, s>>>(src, (float*)p->big, p->N, p->L);
   cudaError_t e = cudaGetLastError();
   if (!e) e = conv2n(p, 3, s);
+  if (p->vis) return e;
   if (!e) {
     k_crop_pad<<<grid_of(big_n), CNT, 0, s>>>((float*)p->big, p->N, p->L);
     e = cudaGetLastError();
@@ -265,6 +267,7 @@ cudaError_t linear_setup(mf_plan* p, const float* psf) {
 }
 
 cudaError_t linear_hty(mf_plan* p, const float* y, cudaStream_t s) {
+  if (p->vis) return vis_dirty(p, y, s);
   const size_t big_n = (size_t)4 * p->cube;
   k_pad<<<grid_of(big_n), CNT, 0, s>>>(y, (float*)p->big, p->N, p->L);
   cudaError_t e = cudaGetLastError();
@@ -311,6 +314,7 @@ cudaError_t linear_fit(mf_plan* p, const float* y, double* partials, int* nblock
   cudaError_t e = cudaGetLastError();
   if (!e) e = conv2n(p, 3, s);
   if (e) return e;
+  if (p->vis) return vis_fit(p, partials, nblocks, s);
   const dim3 g(MF_CG_CHUNKS, p->L);
   k_cg_fit<<<g, CNT, 0, s>>>((const float*)p->big, y, p->N, partials);
   *nblocks = MF_CG_CHUNKS * p->L;

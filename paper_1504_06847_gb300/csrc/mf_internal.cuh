@@ -121,6 +121,17 @@ struct mf_plan {
   double rho_bar;    // rho of Eq. Qlsimp for the current call
   double* cgs;       // per band: gamma, p.q, alpha, beta, gamma' ([5][L])
   double* cgpart;    // per band and chunk partial sums [L][MF_CG_CHUNKS]
+  // visibility operator (plans from mf_plan_create_vis; linear == 1 as well):
+  // h2 holds the transfer function of each band's Toeplitz kernel, cgv[0] the dirty image
+  int vis;
+  std::vector<int> vis_off;  // [L+1] first visibility of each band (host)
+  void* vis_uv;      // [total] float2 (u, v) in cells
+  void* vis_w;       // [total] weights, or null (all 1)
+  double* vis_c0;    // 1/2 sum w |y|^2 of the current call
+  void* vis_phihat;  // [N] kernel transform at the image's modes
+  void* vis_twM;     // twiddles of length 2N (the dirty image's grid)
+  void* vis_spec;    // two planes' half spectra at 2N: [2][2N][N] complex
+  void* vis_nyq;     // their kx = N columns: [2][2N] complex
   size_t total_bytes;
   cudaStream_t stream;
   mf_status status;
@@ -215,6 +226,14 @@ cudaError_t linear_setup(mf_plan* p, const float* psf);
 cudaError_t linear_hty(mf_plan* p, const float* y, cudaStream_t s);
 cudaError_t linear_step_I(mf_plan* p, int cg_iters, double rho_bar, cudaStream_t s);
 cudaError_t linear_fit(mf_plan* p, const float* y, double* partials, int* nblocks, cudaStream_t s);
+
+// Visibility operator (vis.cu): plan-time Toeplitz kernels (into h2), the
+// per-call dirty image Re(Phi^H W y) (into cgv) and 1/2 sum w |y|^2, and the
+// data-fit partials from A X held in big (residual iterations).
+size_t vis_spec_elems(int N);
+cudaError_t vis_setup(mf_plan* p, const int* counts);
+cudaError_t vis_dirty(mf_plan* p, const float* y, cudaStream_t s);
+cudaError_t vis_fit(mf_plan* p, double* partials, int* nblocks, cudaStream_t s);
 
 // Dual residual of residual iterations (dual.cu): cubes of p->dual, the
 // snapshot taken before step I, and the reduction after the iteration.

@@ -95,7 +95,8 @@ void free_plan_memory(mf_plan* p) {
                   p->hhat_nyq,
                   p->yhat, p->yhat_nyq, p->cc, p->cc_nyq, p->gg, p->gg_nyq, p->tw, p->dctC, p->scratch,
                   p->partials, p->sums, p->wset, p->dct_tc, p->err, p->bwd_buf, p->dual, p->h2, p->h2_nyq,
-                  p->tw2, p->work2, p->big, p->cgv, p->cgs, p->cgpart};
+                  p->tw2, p->work2, p->big, p->cgv, p->cgs, p->cgpart, p->vis_uv, p->vis_w, p->vis_c0,
+                  p->vis_phihat, p->vis_twM, p->vis_spec, p->vis_nyq};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   p->bwd_buf = nullptr;
@@ -113,11 +114,13 @@ size_t scratch_elems(int N, int L) {
   return 2 * s * MF_MAX_BASES * L;
 }
 
+// no_psf: a plan whose step I does not use the circulant transfer function
+// (the visibility operator): psf is not read and hhat is zero.
 template <class R>
-mf_status create(int N, int L, const R* psf, mf_plan** out) {
+mf_status create(int N, int L, const R* psf, mf_plan** out, bool no_psf = false) {
   if (!out) return MF_ERR_INVALID;
   *out = nullptr;
-  if (!psf || !is_pow2(N) || N < 16 || N > 2048 || L < 2 || L > MF_MAX_L) return MF_ERR_INVALID;
+  if ((!psf && !no_psf) || !is_pow2(N) || N < 16 || N > 2048 || L < 2 || L > MF_MAX_L) return MF_ERR_INVALID;
   if (sizeof(R) == 8 && L > 64) return MF_ERR_INVALID;
   mf_plan* p = new (std::nothrow) mf_plan();
   if (!p) return MF_ERR_OOM;
@@ -224,13 +227,19 @@ mf_status create(int N, int L, const R* psf, mf_plan** out) {
     }
   }
   // transfer function of every band: F(ifftshift(psf))
-  R* shifted = reinterpret_cast<R*>(p->X);
-  k_shift_psf<R><<<1024, 256>>>(psf, shifted, N, p->cube);
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = launch_rows_fwd<R>(shifted, (cx<R>*)p->work, N, N * L, (const cx<R>*)p->tw, 0);
-  if (e == cudaSuccess)
-    e = launch_cols<R>((cx<R>*)p->work, N, L, (const cx<R>*)p->tw, 0, (cx<R>*)p->hhat, (cx<R>*)p->hhat_nyq,
-                       nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
+  cudaError_t e = cudaSuccess;
+  if (no_psf) {
+    e = cudaMemset(p->hhat, 0, half);
+    if (e == cudaSuccess) e = cudaMemset(p->hhat_nyq, 0, nyq);
+  } else {
+    R* shifted = reinterpret_cast<R*>(p->X);
+    k_shift_psf<R><<<1024, 256>>>(psf, shifted, N, p->cube);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_rows_fwd<R>(shifted, (cx<R>*)p->work, N, N * L, (const cx<R>*)p->tw, 0);
+    if (e == cudaSuccess)
+      e = launch_cols<R>((cx<R>*)p->work, N, L, (const cx<R>*)p->tw, 0, (cx<R>*)p->hhat, (cx<R>*)p->hhat_nyq,
+                         nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
+  }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     free_plan_memory(p);
@@ -650,6 +659,7 @@ void* array_ptr(mf_plan* p, int which, size_t* count) {
     case MF_ARR_GAMMA_S_DCT: return p->GSd;
     case MF_ARR_GAMMA_V2: return p->GV2;
     case MF_ARR_B: return p->b;
+    case MF_ARR_HTY: return p->linear ? p->cgv : nullptr;
     case MF_ARR_GAMMA_T: *count = p->cube * (p->nd_state > 0 ? p->nd_state : MF_MAX_BASES); return p->GT[p->gt_cur];
     default: return nullptr;
   }
@@ -731,6 +741,58 @@ mf_status mf_plan_create_linear(int N, int L, const float* psf_cube, mf_plan** o
   return MF_OK;
 }
 
+mf_status mf_plan_create_vis(int N, int L, const int* n_vis, const float* uv, const float* weights,
+                             mf_plan** out) {
+  if (!out) return MF_ERR_INVALID;
+  *out = nullptr;
+  if (!n_vis || !is_pow2(N) || N < 16 || N > 512 || L < 2 || L > MF_MAX_L) return MF_ERR_INVALID;
+  long total = 0;
+  for (int l = 0; l < L; l++) {
+    if (n_vis[l] < 0) return MF_ERR_INVALID;
+    total += n_vis[l];
+  }
+  if (total > (1L << 30) || (total > 0 && !uv)) return MF_ERR_INVALID;
+  mf_plan* p = nullptr;
+  mf_status st = create<float>(N, L, nullptr, &p, true);
+  if (st != MF_OK) return st;
+  const size_t cb = p->cube * sizeof(float);
+  Alloc a{p};
+  p->h2 = a.get(4 * cb);
+  p->h2_nyq = a.get((size_t)L * 2 * N * sizeof(cx<float>));
+  p->tw2 = a.get((size_t)2 * N * sizeof(cx<float>));
+  p->work2 = a.get(4 * cb);
+  p->big = a.get(4 * cb);
+  p->cgv = a.get(4 * cb);
+  p->cgs = (double*)a.get((size_t)5 * L * sizeof(double));
+  p->cgpart = (double*)a.get((size_t)MF_CG_CHUNKS * L * sizeof(double));
+  if (total > 0) p->vis_uv = a.get(sizeof(float2) * total);
+  if (total > 0 && weights) p->vis_w = a.get(sizeof(float) * total);
+  p->vis_c0 = (double*)a.get(sizeof(double));
+  p->vis_phihat = a.get(sizeof(float) * N);
+  p->vis_twM = a.get((size_t)2 * N * sizeof(cx<float>));
+  p->vis_spec = a.get(vis_spec_elems(N) * sizeof(cx<float>));
+  p->vis_nyq = a.get((size_t)2 * 2 * N * sizeof(cx<float>));
+  if (!a.ok) {
+    mf_plan_destroy(p);
+    return MF_ERR_OOM;
+  }
+  p->linear = 1;
+  p->vis = 1;
+  p->vis_off.assign(L + 1, 0);
+  for (int l = 0; l < L; l++) p->vis_off[l + 1] = p->vis_off[l] + n_vis[l];
+  cudaError_t e = cudaSuccess;
+  if (total > 0) e = cudaMemcpy(p->vis_uv, uv, sizeof(float2) * total, cudaMemcpyDeviceToDevice);
+  if (!e && total > 0 && weights) e = cudaMemcpy(p->vis_w, weights, sizeof(float) * total, cudaMemcpyDeviceToDevice);
+  if (!e) e = vis_setup(p, n_vis);
+  if (e) {
+    cudaGetLastError();
+    mf_plan_destroy(p);
+    return e == cudaErrorInvalidValue ? MF_ERR_INVALID : MF_ERR_CUDA;
+  }
+  *out = p;
+  return MF_OK;
+}
+
 void mf_plan_destroy(mf_plan* p) {
   if (!p) return;
   cudaDeviceSynchronize();
@@ -766,7 +828,7 @@ mf_status mf_plan_get_array(mf_plan* p, int which, void* dst, size_t* count) {
 }
 
 mf_status mf_plan_set_array(mf_plan* p, int which, const void* src, size_t count) {
-  if (!p || !src) return MF_ERR_INVALID;
+  if (!p || !src || which == MF_ARR_HTY) return MF_ERR_INVALID;
   size_t n = 0;
   void* dst = array_ptr(p, which, &n);
   if (which == MF_ARR_GAMMA_T) n = p->cube * MF_MAX_BASES;

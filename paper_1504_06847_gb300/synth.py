@@ -34,7 +34,10 @@ consumer sees the same coordinates), the exact sum
 ``sum_{r,c} x[r][c] exp(-2 pi i (u (c - N/2) + v (r - N/2)) / N)`` plus complex
 white noise (each part of standard deviation ``sigma/sqrt(2)``,
 ``sigma = rms|Phi x| * 10^(-snr_db/20)``), and weights 1 or, with
-``random_weights``, ``U(0.5, 1.5)``.
+``random_weights``, ``U(0.5, 1.5)``, divided by their sum in each band, so that
+the dirty beam ``sum_m w_m exp(2 pi i u_m . d / N)`` peaks at 1 like the PSF of
+step 3 (and ``Re(Phi^H W Phi) + rho I`` stays as well conditioned as in the
+image-domain workloads).
 """
 
 from __future__ import annotations
@@ -118,6 +121,7 @@ def make_visibilities(N: int, L: int, n_sources: int, n_antennas: int, seed: int
         weights = [rng.uniform(0.5, 1.5, size=len(v)) for v in vis]
     else:
         weights = [np.ones(len(v)) for v in vis]
+    weights = [a / a.sum() if len(a) else a for a in weights]
     return Visibilities(sky=sky, uv=uvs, vis=vis, weights=weights, nu=nu, sigma=sigma)
 
 

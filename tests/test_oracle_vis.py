@@ -196,6 +196,7 @@ def test_synthetic_visibilities_follow_the_recipe():
     for l, q in enumerate(c.uv):
         assert np.all(np.abs(q) < 0.4 * 32 + 1e-9)  # |p_i - p_j| <= 2, nu / nu0 <= 2, N / 10
         assert np.array_equal(q, q.astype(np.float32).astype(np.float64))
+        assert abs(c.weights[l].sum() - 1.0) < 1e-12  # dirty beam peak 1
     # noise at 20 dB: the clean part is the oracle's forward operator
     pb = oracle.Problem.visibilities(32, c.uv, c.vis, PRM, J=2)
     clean = pb.apply_H(c.sky)
