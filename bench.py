@@ -38,6 +38,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -359,6 +361,109 @@ def measure_forms(stream, xstep_ms=None):
     return out
 
 
+# Bytes per voxel of the N x N cube moved by one conjugate-gradient iteration of
+# step I (FP32; the 2N x 2N images hold 4 values per voxel).  One 2N
+# convolution: row transform 16 in + 16 out, column pass (spectrum in and out,
+# transfer function in) 48, inverse rows 16 + 16: 112.  Zero padding writes 16
+# (reads 4); the crop-and-pad of the linear operator reads and writes 32.  The
+# CG vector updates (q, X and r, p) move 48.  Linear convolution: two
+# convolutions per operator application; visibilities: one.
+CG_BYTES = {"linear": 20 + 112 + 32 + 112 + 48, "vis": 20 + 112 + 48}
+# the spectral step with the Chebyshev basis added: X in; Gamma_P, S, Gamma_V,
+# Gamma_V2, Gamma_S in and out; b out
+SPECTRAL_B2_BYTES = 4 + 5 * 8 + 4
+
+
+def measure_widened_rows(stream, plan, y, peak):
+    """The rows beyond the benchmark's path, each timed with CUDA events (per-kernel
+    events inside the library) on `stream`: the Chebyshev spectral dictionary and
+    the spectral-index fit on the benchmark cube, step I by conjugate gradients for
+    a linear convolution and for visibilities at 512 x 512 x 32."""
+    import torch
+
+    import paper_1504_06847_gb300 as mf
+    from paper_1504_06847_gb300 import synth
+
+    prm = synth.WORKLOAD_PARAMS
+    out = {}
+    N, L = plan.N, plan.L
+    V = N * N * L
+    with torch.cuda.stream(stream):
+        # DCT alone (FP32) and DCT + Chebyshev, 10 iterations each, same cube
+        rows = {}
+        for mask in (1, 3):
+            kw = dict(prm, stream=stream.cuda_stream, precision=mf.MF_FP32, spectral_mask=mask)
+            plan.iterate(y, 2, **kw)
+            plan.set_timing(True)
+            s, e = _events(torch)
+            s.record(stream)
+            plan.iterate(y, 10, **dict(kw, warm_start=1))
+            e.record(stream)
+            stream.synchronize()
+            t = plan.timing()
+            plan.set_timing(False)
+            sp_ms, sp_n = t["spectral"]
+            b = (SPECTRAL_B2_BYTES if mask == 3 else 40) * V
+            rows[mask] = {"ms_per_iteration": s.elapsed_time(e) / 10, "spectral_ms_per_launch": sp_ms / sp_n,
+                          "spectral_alg_bytes_per_launch": b,
+                          "spectral_achieved_gbs": b / (sp_ms / sp_n * 1e-3) / 1e9,
+                          "spectral_frac": b / (sp_ms / sp_n * 1e-3) / 1e9 / peak}
+        out["chebyshev_dictionary"] = {"workload": f"{N}x{N}x{L}", "dct_only_fp32": rows[1],
+                                       "dct_and_chebyshev_fp32": rows[3], "dtype": "f32"}
+        # spectral-index fit of the reconstructed cube
+        x = plan.x()
+        nu = 1.0 + np.arange(L) / (L - 1)
+        mf.spectral_index(x, nu, stream=stream.cuda_stream)
+        s, e = _events(torch)
+        s.record(stream)
+        for _ in range(10):
+            mf.spectral_index(x, nu, stream=stream.cuda_stream)
+        e.record(stream)
+        stream.synchronize()
+        t_si = s.elapsed_time(e) / 10
+        b = (L + 3) * N * N * 4
+        out["spectral_index"] = {"workload": f"{N}x{N}x{L}", "ms": t_si, "alg_bytes": b,
+                                 "achieved_gbs": b / (t_si * 1e-3) / 1e9, "frac": b / (t_si * 1e-3) / 1e9 / peak}
+        # step I by conjugate gradients: linear convolution and visibilities
+        n2, l2, cg, n_it = 512, 32, 10, 5
+        c = synth.make_cube(n2, l2, n_sources=40, n_antennas=128, seed=12)
+        lin = mf.Plan(torch.tensor(c.psf, dtype=torch.float32, device="cuda"), linear=True)
+        yl = torch.tensor(c.y, dtype=torch.float32, device="cuda")
+        cv = synth.make_visibilities(n2, l2, n_sources=40, n_antennas=128, seed=13, random_weights=True)
+        t0 = time.perf_counter()
+        vis = mf.Plan.from_visibilities(n2, [torch.tensor(q, dtype=torch.float32, device="cuda") for q in cv.uv],
+                                        [torch.tensor(w, dtype=torch.float32, device="cuda") for w in cv.weights])
+        torch.cuda.synchronize()
+        t_create = (time.perf_counter() - t0) * 1e3
+        yv = torch.tensor(np.concatenate(cv.vis).astype(np.complex64), device="cuda")
+        for name, p_, yy in (("linear", lin, yl), ("vis", vis, yv)):
+            kw = dict(prm, stream=stream.cuda_stream, cg_iters=cg)
+            p_.iterate(yy, 2, **kw)
+            p_.set_timing(True)
+            s, e = _events(torch)
+            s.record(stream)
+            p_.iterate(yy, n_it, **kw)
+            e.record(stream)
+            stream.synchronize()
+            t = p_.timing()
+            p_.set_timing(False)
+            v2 = n2 * n2 * l2
+            cg_ms = t["cg"][0] / n_it
+            b = (cg + 1) * CG_BYTES[name] * v2
+            row = {"workload": f"{n2}x{n2}x{l2}", "cg_iters": cg, "ms_per_iteration": s.elapsed_time(e) / n_it,
+                   "step_I_ms": cg_ms, "step_I_alg_bytes": b, "step_I_achieved_gbs": b / (cg_ms * 1e-3) / 1e9,
+                   "step_I_frac": b / (cg_ms * 1e-3) / 1e9 / peak,
+                   "per_call_setup_ms": t["setup"][0] / max(1, t["setup"][1]),
+                   "voxel_it_per_s": v2 * n_it / (s.elapsed_time(e) * 1e-3), "dtype": "f32"}
+            if name == "vis":
+                row.update({"visibilities": int(yv.shape[0]), "plan_create_ms": t_create,
+                            "note": "per_call_setup_ms is the gridded dirty image Re(Phi^H W y)"})
+            out[f"{name}_cg"] = row
+        lin.close()
+        vis.close()
+    return out
+
+
 def xstep_reference(stream, ours_ms):
     """Step I of the benchmarked cube with cuFFT (torch.fft: rfft2, the filter,
     irfft2), a reference point only: it is not on this library's path."""
@@ -591,6 +696,7 @@ def main():
     if not args.no_forms:
         xs = sum(per_kernel[k]["ms_per_launch"] for k in ("rows_fwd", "cols_solve", "rows_inv"))
         line["forms"] = measure_forms(stream, xs)
+        line["widened_rows"] = measure_widened_rows(stream, plan, y, peak)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cube)
     print(json.dumps(line), flush=True)
