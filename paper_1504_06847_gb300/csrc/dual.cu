@@ -12,20 +12,18 @@
 // Before step I the plan keeps pre = b - Gamma_P and the DCT-domain S W_nu and
 // Gamma_S W_nu; after the iteration
 //   acc = (b - Gamma_P) - pre - (dGamma_S W_nu) W_nu^T          (per pixel spectrum)
-//   acc -= w_k W_k^T (Gamma_T,k+ - Gamma_T,k)                    (each distinct basis)
-// and the report's dual residual is ||acc||^2 + rho_V^2 ||d(S W_nu)||^2 (W_nu
-// orthonormal).  Both Gamma_T buffers are complete states, so the change of
-// every coefficient is at hand without extra storage.
+//   acc += sum_k w_k W_k^T (Gamma_T,k - Gamma_T,k+)              (every distinct basis)
+// and the report's dual residual is ||acc||^2 + m_nu rho_V^2 ||d(S W_nu)||^2
+// (orthonormal spectral bases).  Both Gamma_T buffers are complete states, so
+// the change of every coefficient is at hand without extra storage; the
+// synthesis runs the fused level kernels in their synthesis-only mode
+// (wavelet.cu), level by level, through the level scratch of the iteration.
 #include <cuda_runtime.h>
 
 #include "mf_internal.cuh"
 #include "reduce.cuh"
 
 namespace mf {
-
-template <class R>
-cudaError_t launch_wav_synthesis_acc(R* coef, R* out, R* tmp, int N, int L, int J, int nd, const int* Ks,
-                                     cudaStream_t s);
 
 namespace {
 
@@ -86,14 +84,6 @@ __global__ void __launch_bounds__(DNT) k_dual_spec(const R* __restrict__ b, cons
   block_reduce_write<DNT>(q, partials + (size_t)blockIdx.x * MF_NQ);
 }
 
-// work = -w (Gamma_T+ - Gamma_T) of one basis (all levels of every band)
-template <class R>
-__global__ void k_dual_gdiff(const R* __restrict__ gn, const R* __restrict__ go, R* __restrict__ work, R w,
-                             size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    work[i] = -w * (gn[i] - go[i]);
-}
-
 template <class R>
 __global__ void __launch_bounds__(DNT) k_dual_norm(const R* __restrict__ acc, size_t n,
                                                     double* __restrict__ partials) {
@@ -110,7 +100,7 @@ __global__ void __launch_bounds__(DNT) k_dual_norm(const R* __restrict__ acc, si
 
 }  // namespace
 
-size_t dual_cubes() { return 5; }  // pre, S W_nu and Gamma_S W_nu snapshots, basis work cube, synthesis scratch
+size_t dual_cubes() { return 3; }  // pre (then acc), S W_nu and Gamma_S W_nu snapshots
 
 template <class R>
 cudaError_t dual_snapshot(mf_plan* p, cudaStream_t s) {
@@ -124,12 +114,11 @@ cudaError_t dual_snapshot(mf_plan* p, cudaStream_t s) {
 }
 
 template <class R>
-cudaError_t dual_finish(mf_plan* p, const R* gt_old, const R* gt_new, int J, int nd, const int* Ks, const R* w,
-                        cudaStream_t s) {
+cudaError_t dual_spectral(mf_plan* p, cudaStream_t s) {
   R* base = (R*)p->dual;
   const size_t V = p->cube;
   const int N = p->N, L = p->L, NN = N * N;
-  R *pre = base, *Sd0 = base + V, *GSd0 = base + 2 * V, *work = base + 3 * V, *tmp = base + 4 * V;
+  R *pre = base, *Sd0 = base + V, *GSd0 = base + 2 * V;
   const size_t sm = sizeof(R) * ((size_t)L * L + (size_t)L * DPIX);
   cudaError_t e = cudaFuncSetAttribute(k_dual_spec<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e) return e;
@@ -137,25 +126,31 @@ cudaError_t dual_finish(mf_plan* p, const R* gt_old, const R* gt_new, int J, int
   k_dual_spec<R><<<gs, DNT, sm, s>>>((const R*)p->b, (const R*)p->GP, pre, (const R*)p->Sd, Sd0, (const R*)p->GSd,
                                      GSd0, (const R*)p->dctC, NN, L, p->partials);
   if ((e = cudaGetLastError())) return e;
-  if ((e = launch_finalize(p->partials, (int)gs, p->sums, 1, s))) return e;
-  for (int k = 0; k < nd && !e; k++) {
-    const unsigned g = capped_grid((V + DNT - 1) / DNT);
-    k_dual_gdiff<R><<<g, DNT, 0, s>>>(gt_new + (size_t)k * V, gt_old + (size_t)k * V, work, w[k], V);
-    e = cudaGetLastError();
-    if (!e) e = launch_wav_synthesis_acc<R>(work, pre, tmp, N, L, J, 1, Ks + k, s);
-  }
-  if (e) return e;
+  return launch_finalize(p->partials, (int)gs, p->sums, 1, s);
+}
+
+template <class R>
+R* dual_acc(mf_plan* p) {
+  return (R*)p->dual;
+}
+
+template <class R>
+cudaError_t dual_norm(mf_plan* p, cudaStream_t s) {
+  const size_t V = p->cube;
   const unsigned gn = capped_grid((V + DNT - 1) / DNT);
-  k_dual_norm<R><<<gn, DNT, 0, s>>>(pre, V, p->partials);
-  if ((e = cudaGetLastError())) return e;
+  k_dual_norm<R><<<gn, DNT, 0, s>>>((const R*)p->dual, V, p->partials);
+  cudaError_t e = cudaGetLastError();
+  if (e) return e;
   return launch_finalize(p->partials, (int)gn, p->sums, 1, s);
 }
 
 template cudaError_t dual_snapshot<float>(mf_plan*, cudaStream_t);
 template cudaError_t dual_snapshot<double>(mf_plan*, cudaStream_t);
-template cudaError_t dual_finish<float>(mf_plan*, const float*, const float*, int, int, const int*, const float*,
-                                        cudaStream_t);
-template cudaError_t dual_finish<double>(mf_plan*, const double*, const double*, int, int, const int*,
-                                         const double*, cudaStream_t);
+template cudaError_t dual_spectral<float>(mf_plan*, cudaStream_t);
+template cudaError_t dual_spectral<double>(mf_plan*, cudaStream_t);
+template float* dual_acc<float>(mf_plan*);
+template double* dual_acc<double>(mf_plan*);
+template cudaError_t dual_norm<float>(mf_plan*, cudaStream_t);
+template cudaError_t dual_norm<double>(mf_plan*, cudaStream_t);
 
 }  // namespace mf

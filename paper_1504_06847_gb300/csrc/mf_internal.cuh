@@ -194,6 +194,9 @@ template <class R> cudaError_t launch_wav_ll(const R* in, size_t in_band_stride,
 // Fused level: analysis of the M x M input, thresholds and dual update of the level's
 // coefficients, synthesis into the M x M output (or accumulation into b at level 1).
 // pref_tile: preferred output tile edge (64 or 32) where the level is large enough.
+// resid: 0 plain, 1 with the residual partials, 2 synthesis only (no input, no
+// update): the level's coefficients are gt_old - gt_new, rcoarse the low-low
+// band below the coarsest level; out receives the synthesis (level 1: added).
 template <class R> cudaError_t launch_wav_level(const R* in, size_t in_band_stride, size_t in_basis_stride,
                                                 const R* rcoarse, R* out, const R* gt_old, R* gt_new,
                                                 int N, int M, int L, int coarsest, int nd, const WavSet<R>* ws,
@@ -239,7 +242,11 @@ cudaError_t vis_fit(mf_plan* p, double* partials, int* nblocks, cudaStream_t s);
 // snapshot taken before step I, and the reduction after the iteration.
 size_t dual_cubes();
 template <class R> cudaError_t dual_snapshot(mf_plan* p, cudaStream_t s);
-template <class R> cudaError_t dual_finish(mf_plan* p, const R* gt_old, const R* gt_new, int J, int nd,
-                                           const int* Ks, const R* w, cudaStream_t s);
+// After the iteration: the spectral part of acc and ||dS||^2 (dual_spectral),
+// the wavelet part added into acc by the level kernels' synthesis-only mode,
+// then ||acc||^2 (dual_norm).
+template <class R> cudaError_t dual_spectral(mf_plan* p, cudaStream_t s);
+template <class R> R* dual_acc(mf_plan* p);
+template <class R> cudaError_t dual_norm(mf_plan* p, cudaStream_t s);
 
 }  // namespace mf

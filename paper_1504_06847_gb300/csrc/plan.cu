@@ -433,10 +433,20 @@ cudaError_t iteration(mf_plan* p, int J, const WavSet<R>& ws, const WavSet<R>* w
     }
   }
   if (resid) {
+    // dual residual: acc = d(b - Gamma_P) - dGamma_S - sum_k w_k W_k^T dGamma_T,k, the
+    // wavelet term synthesised level by level from the two Gamma_T buffers through
+    // the (now free) level scratch RC
     Timed t(p, MF_K_DUAL, s);
-    int Ks[MF_MAX_BASES];
-    for (int k = 0; k < nd; k++) Ks[k] = ws.K[k];
-    if ((e = dual_finish<R>(p, gto, gtn, J, nd, Ks, ws.w, s))) return e;
+    if ((e = dual_spectral<R>(p, s))) return e;
+    for (int j = J; j >= 1; j--) {
+      const int M = N >> (j - 1);
+      const R* rco = j == J ? nullptr : RC[j];
+      R* outp = j == 1 ? dual_acc<R>(p) : RC[j - 1];
+      if ((e = launch_wav_level<R>(nullptr, 0, 0, rco, outp, gto, gtn, N, M, L, j == J, nd, wsd, sc, nullptr, 2,
+                                   p->wav_tile, p->err, s)))
+        return e;
+    }
+    if ((e = dual_norm<R>(p, s))) return e;
   }
   p->gt_cur = 1 - p->gt_cur;
   return cudaSuccess;

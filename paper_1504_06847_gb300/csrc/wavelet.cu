@@ -113,6 +113,9 @@ __device__ __forceinline__ void load_tile(const R* __restrict__ img, int M, int 
 // Coefficients of this level live in the top-left M x M block of the band's
 // Gamma_T image (pitch N).  rco: the M/2 x M/2 coarse reconstruction used as the
 // low-low band (nullptr at the coarsest level, whose low-low band is thresholded).
+// RESID: 0 plain, 1 with the residual terms, 2 synthesis only (no input tile):
+// the level's coefficients are gto - gtn (the change of Gamma_T over the
+// iteration, negated), with rco as the low-low band below the coarsest level.
 template <class R, int K, int RESID, class Emit>
 __device__ __forceinline__ void level_tile(const R* in, int off, int T, R* ra, R* rd, R* sb,
                                            const R* __restrict__ h, const R* __restrict__ g, int M, int y0, int x0,
@@ -130,7 +133,7 @@ __device__ __forceinline__ void level_tile(const R* in, int off, int T, R* ra, R
     gr[n] = g[n];
   }
   // 1. row analysis of IH input rows into CW low and CW high coefficients
-  for (int e = tid; e < IH * CW; e += WNT) {
+  for (int e = tid; e < (RESID == 2 ? 0 : IH * CW); e += WNT) {
     const int r = e / CW, c = e % CW;
     const R* src = in + (off + r) * IHM + off + 2 * c;
     R a = 0, d = 0;
@@ -145,7 +148,7 @@ __device__ __forceinline__ void level_tile(const R* in, int off, int T, R* ra, R
   }
   __syncthreads();
   // 2. column analysis: four sub-bands of CW x CW coefficients
-  for (int e = tid; e < CW * CW; e += WNT) {
+  for (int e = tid; e < (RESID == 2 ? 0 : CW * CW); e += WNT) {
     const int i = e / CW, c = e % CW;
     R s00 = 0, s01 = 0, s10 = 0, s11 = 0;
 #pragma unroll
@@ -173,6 +176,9 @@ __device__ __forceinline__ void level_tile(const R* in, int off, int T, R* ra, R
     R* cell = sb + qd * CWM * CWM + i * CWM + c;
     if (qd == 0 && rco != nullptr) {
       *cell = rco[(size_t)gi * Mh + gc];
+    } else if (RESID == 2) {
+      const size_t pos = (size_t)(gi + (qd >> 1) * Mh) * N + gc + (qd & 1) * Mh;
+      *cell = gto[pos] - gtn[pos];
     } else {
       const size_t pos = (size_t)(gi + (qd >> 1) * Mh) * N + gc + (qd & 1) * Mh;
       const R z = *cell;
@@ -183,7 +189,7 @@ __device__ __forceinline__ void level_tile(const R* in, int off, int T, R* ra, R
       *cell = gn + sc.rho_T * tp;
       if (i >= own0 && i < own1 && c >= own0 && c < own1) {
         gtn[pos] = gn;
-        if (RESID) {
+        if (RESID == 1) {
           const double dg = (double)gn - (double)gam;
           q[Q_DGT] += (double)w * dg * dg;
           q[Q_L1S] += (double)w * fabs((double)z);
@@ -272,8 +278,9 @@ __global__ void __launch_bounds__(WNT) k_wav_level1(const R* __restrict__ X, R* 
   const int band = blockIdx.y;
   const int y0 = (blockIdx.x / tpd) * T, x0 = (blockIdx.x % tpd) * T;
   const size_t NN = (size_t)N * N;
-  load_tile<R>(X + band * NN, N, y0 - 2 * MF_MAX_K + 2, x0 - 2 * MF_MAX_K + 2, T + 4 * MF_MAX_K - 4,
-               T + 4 * MF_MAX_K - 4, in, IHM);
+  if (RESID != 2)
+    load_tile<R>(X + band * NN, N, y0 - 2 * MF_MAX_K + 2, x0 - 2 * MF_MAX_K + 2, T + 4 * MF_MAX_K - 4,
+                 T + 4 * MF_MAX_K - 4, in, IHM);
   __syncthreads();
   double q[Q_COUNT];
 #pragma unroll
@@ -300,7 +307,7 @@ __global__ void __launch_bounds__(WNT) k_wav_level1(const R* __restrict__ X, R* 
       b[o] = b[o] + acc[s];
     }
   }
-  if (RESID) block_reduce_write<WNT>(q, partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * MF_NQ);
+  if (RESID == 1) block_reduce_write<WNT>(q, partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * MF_NQ);
 }
 
 // Level j >= 2 (M = N / 2^(j-1)): one basis per CTA; writes R_{j-1} (M x M).
@@ -317,7 +324,7 @@ __global__ void __launch_bounds__(WNT) k_wav_levelj(const R* __restrict__ in_img
   const int band = blockIdx.y, k = blockIdx.z;
   const int y0 = (blockIdx.x / tpd) * T, x0 = (blockIdx.x % tpd) * T;
   const size_t MM = (size_t)M * M;
-  const R* src = in_img + ((size_t)k * L + band) * MM;
+  const R* src = RESID == 2 ? nullptr : in_img + ((size_t)k * L + band) * MM;
   R* dst = out_img + ((size_t)k * L + band) * MM;
   const size_t gofs = ((size_t)k * L + band) * (size_t)N * N;
   const R* rc = coarsest ? nullptr : rco + ((size_t)k * L + band) * (MM / 4);
@@ -328,12 +335,12 @@ __global__ void __launch_bounds__(WNT) k_wav_levelj(const R* __restrict__ in_img
   const R w = ws->w[k];
   auto emit = [&](int, int m, int x, R v) { dst[(size_t)(y0 + m) * M + x0 + x] = v; };
   MF_K_SWITCH(ws->K[k], {
-    load_tile<R>(src, M, y0 - 2 * KK + 2, x0 - 2 * KK + 2, T + 4 * KK - 4, T + 4 * KK - 4, in, IHM);
+    if (RESID != 2) load_tile<R>(src, M, y0 - 2 * KK + 2, x0 - 2 * KK + 2, T + 4 * KK - 4, T + 4 * KK - 4, in, IHM);
     __syncthreads();
     level_tile<R, KK, RESID>(in, 0, T, ra, rd, sb, ws->h[k], ws->g[k], M, y0, x0, gto + gofs, gtn + gofs, N, rc, sc,
                              w, q, emit);
   });
-  if (RESID)
+  if (RESID == 1)
     block_reduce_write<WNT>(
         q, partials + (((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * MF_NQ);
 }
@@ -475,8 +482,9 @@ __device__ __forceinline__ void level_tile_t(const R* in, int off, R* rpair, R* 
   P* bot = top + C::SR * B_CP;           // {bottom-left, bottom-right}: high rows
   const int tid = threadIdx.x;
   // 1. row analysis: row r, coefficient pairs {low, high} RB j..RB j+RB-1;
-  //    consecutive threads take consecutive rows
-  for (int it = tid; it < IH * NRUN; it += WNT) {
+  //    consecutive threads take consecutive rows (none in the synthesis-only
+  //    mode, RESID == 2, which has no input tile; see level_tile)
+  for (int it = tid; it < (RESID == 2 ? 0 : IH * NRUN); it += WNT) {
     const int r = it % IH, j = it / IH;
     const R* src = in + (off + r) * B_IP + off + 2 * RB * j;
     R v[NV];
@@ -508,6 +516,28 @@ __device__ __forceinline__ void level_tile_t(const R* in, int off, R* rpair, R* 
     const int Mh = M / 2;
     const int ci0 = y0 / 2 - (K - 1), cj0 = x0 / 2 - (K - 1);
     const int MhN = Mh * N;
+    if constexpr (RESID == 2) {
+      // synthesis only: the four sub-bands are gto - gtn (rco as the low-low band)
+      for (int it = tid; it < CW * NRUN2; it += WNT) {
+        const int c = it % CW, j = it / CW;
+        const int gc = (cj0 + c) & (Mh - 1);
+#pragma unroll
+        for (int i = 0; i < RB2; i++) {
+          const int row = RB2 * j + i;
+          R tl = 0, tr = 0, bl = 0, br = 0;
+          if (row < CW) {
+            const int gi = (ci0 + row) & (Mh - 1);
+            const int go = gi * N + gc;
+            tl = rco != nullptr ? rco[gi * Mh + gc] : gto[go] - gtn[go];
+            tr = gto[go + Mh] - gtn[go + Mh];
+            bl = gto[go + MhN] - gtn[go + MhN];
+            br = gto[go + MhN + Mh] - gtn[go + MhN + Mh];
+          }
+          top[row * B_CP + c] = mk2(tl, tr);
+          bot[row * B_CP + c] = mk2(bl, br);
+        }
+      }
+    } else
     for (int it = tid; it < CW * NRUN2; it += WNT) {
       const int c = it % CW, j = it / CW;
       const int gc = (cj0 + c) & (Mh - 1);
@@ -540,7 +570,7 @@ __device__ __forceinline__ void level_tile_t(const R* in, int off, R* rpair, R* 
         const R gn = gam + sc.rho_T * (tp - z);
         if (own) {
           gtn[pos] = gn;
-          if (RESID) {
+          if (RESID == 1) {
             const R dg = gn - gam;
             r_dg = fma(dg, dg, r_dg);
             r_l1 += fabs(z);
@@ -563,7 +593,7 @@ __device__ __forceinline__ void level_tile_t(const R* in, int off, R* rpair, R* 
         top[row * B_CP + c] = mk2(tl, update(lo.y, gtr[i], own, go[i] + Mh));
         bot[row * B_CP + c] = mk2(update(hi.x, gbl[i], own, go[i] + MhN), update(hi.y, gbr[i], own, go[i] + MhN + Mh));
       }
-      if (RESID) {
+      if (RESID == 1) {
         q[Q_DGT] += (double)w * (double)r_dg;
         q[Q_L1S] += (double)w * (double)r_l1;
         if (r_bad) q[Q_NONFIN] += 1.0;
@@ -694,7 +724,7 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_level1_t(const R* __re
   const int band = blockIdx.y;
   const int y0 = (blockIdx.x / tpd) * T, x0 = (blockIdx.x % tpd) * T;
   const size_t NN = (size_t)N * N;
-  load_tile_t<R, T>(X + band * NN, N, y0 - 2 * MF_MAX_K + 2, x0 - 2 * MF_MAX_K + 2, C::IR, in);
+  if (RESID != 2) load_tile_t<R, T>(X + band * NN, N, y0 - 2 * MF_MAX_K + 2, x0 - 2 * MF_MAX_K + 2, C::IR, in);
   cp_async_wait_all();
   for (int r = threadIdx.x; r < T * (T / 32); r += WNT)  // the b tile read at the end
     prefetch_l2(b + band * NN + (size_t)(y0 + r / (T / 32)) * N + x0 + 32 * (r % (T / 32)));
@@ -719,6 +749,7 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_level1_t(const R* __re
       const size_t g1 = ((size_t)(k + 1) * L + band) * NN;
       prefetch_level<R, T>(ws->K[k + 1], gto + g1,
                            coarsest ? nullptr : rco + ((size_t)(k + 1) * L + band) * (NN / 4), N, N, y0, x0);
+      if (RESID == 2) prefetch_level<R, T>(ws->K[k + 1], gtn + g1, nullptr, N, N, y0, x0);
     }
     MF_K_SWITCH(ws->K[k], (level1_basis<R, T, KK, RESID>(in, ra, sb, bacc, N, y0, x0, gto + gofs, gtn + gofs,
                                                          rc, sc, w, q)));
@@ -729,7 +760,7 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_level1_t(const R* __re
     R* dst = b + band * NN + (size_t)(y0 + m) * N + x0 + x;
     *dst += bacc[m * C::BP + x];
   }
-  if (RESID) {
+  if (RESID == 1) {
     R qr[Q_COUNT];  // FP32 plans take the FP32 warp stage of the reduction
 #pragma unroll
     for (int i = 0; i < Q_COUNT; i++) qr[i] = (R)q[i];
@@ -795,18 +826,21 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_levelj_t(const R* __re
   const int per = (ws->nd + gridDim.z - 1) / gridDim.z;
   const int kb = blockIdx.z * per;
   const int ke = kb + per < ws->nd ? kb + per : ws->nd;
-  auto src_of = [&](int k) { return in_img + ((size_t)k * L + band) * MM; };
+  auto src_of = [&](int k) { return RESID == 2 ? (const R*)nullptr : in_img + ((size_t)k * L + band) * MM; };
   auto rc_of = [&](int k) { return coarsest ? (const R*)nullptr : rco + ((size_t)k * L + band) * (MM / 4); };
   if (kb < ke) {
     const int K0 = ws->K[kb];
-    load_tile_t<R, T>(src_of(kb), M, y0 - 2 * K0 + 2, x0 - 2 * K0 + 2, T + 4 * K0 - 4, in);
+    if (RESID != 2) load_tile_t<R, T>(src_of(kb), M, y0 - 2 * K0 + 2, x0 - 2 * K0 + 2, T + 4 * K0 - 4, in);
     prefetch_level<R, T>(K0, gto + ((size_t)kb * L + band) * NN, rc_of(kb), M, N, y0, x0);
+    if (RESID == 2) prefetch_level<R, T>(K0, gtn + ((size_t)kb * L + band) * NN, nullptr, M, N, y0, x0);
   }
   for (int k = kb; k < ke; k++) {
     const bool more = k + 1 < ke;
     if (more) {
-      prefetch_tile<R, T>(src_of(k + 1), M, ws->K[k + 1], y0, x0);
+      if (RESID != 2) prefetch_tile<R, T>(src_of(k + 1), M, ws->K[k + 1], y0, x0);
       prefetch_level<R, T>(ws->K[k + 1], gto + ((size_t)(k + 1) * L + band) * NN, rc_of(k + 1), M, N, y0, x0);
+      if (RESID == 2)
+        prefetch_level<R, T>(ws->K[k + 1], gtn + ((size_t)(k + 1) * L + band) * NN, nullptr, M, N, y0, x0);
     }
     cp_async_wait_all();  // this basis's tile
     __syncthreads();
@@ -817,7 +851,7 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_levelj_t(const R* __re
                                                          more ? ws->K[k + 1] : 0)));
     __syncthreads();
   }
-  if (RESID) {
+  if (RESID == 1) {
     R qr[Q_COUNT];  // FP32 plans take the FP32 warp stage of the reduction
 #pragma unroll
     for (int i = 0; i < Q_COUNT; i++) qr[i] = (R)q[i];
@@ -1312,6 +1346,9 @@ static cudaError_t launch_level_t(const R* in, const R* rcoarse, R* out, const R
   if (M == N) {
     dim3 grid(tiles, L);
     const size_t sm1 = sizeof(R) * TC<T>::SMEM1;
+    if (resid == 2)
+      return launch_k<R>(k_wav_level1_t<R, T, 2>, grid, sm1, s, in, out, gt_old, gt_new, rcoarse, N, L, coarsest, ws,
+                         sc, partials);
     if (resid)
       return launch_k<R>(k_wav_level1_t<R, T, 1>, grid, sm1, s, in, out, gt_old, gt_new, rcoarse, N, L, coarsest, ws,
                          sc, partials);
@@ -1320,6 +1357,9 @@ static cudaError_t launch_level_t(const R* in, const R* rcoarse, R* out, const R
   }
   dim3 grid(tiles, L, levelj_groups(tiles, L, nd));
   const size_t sm = sizeof(R) * TC<T>::SMEM;
+  if (resid == 2)
+    return launch_k<R>(k_wav_levelj_t<R, T, 2>, grid, sm, s, in, out, gt_old, gt_new, rcoarse, N, M, L, coarsest, ws,
+                       sc, partials);
   if (resid)
     return launch_k<R>(k_wav_levelj_t<R, T, 1>, grid, sm, s, in, out, gt_old, gt_new, rcoarse, N, M, L, coarsest, ws,
                        sc, partials);
@@ -1340,6 +1380,9 @@ cudaError_t launch_wav_level(const R* in, size_t, size_t, const R* rcoarse, R* o
   const size_t sm = sizeof(R) * (IHM * IHM + 2 * IHM * CWM + 4 * CWM * CWM);
   if (M == N) {
     dim3 grid(tiles, L);
+    if (resid == 2)
+      return launch_k<R>(k_wav_level1<R, 2>, grid, sm, s, in, out, gt_old, gt_new, rcoarse, N, L, coarsest, ws, sc,
+                         partials);
     if (resid)
       return launch_k<R>(k_wav_level1<R, 1>, grid, sm, s, in, out, gt_old, gt_new, rcoarse, N, L, coarsest, ws, sc,
                          partials);
@@ -1347,6 +1390,9 @@ cudaError_t launch_wav_level(const R* in, size_t, size_t, const R* rcoarse, R* o
                        partials);
   }
   dim3 grid(tiles, L, nd);
+  if (resid == 2)
+    return launch_k<R>(k_wav_levelj<R, 2>, grid, sm, s, in, out, gt_old, gt_new, rcoarse, N, M, L, coarsest, ws, sc,
+                       partials);
   if (resid)
     return launch_k<R>(k_wav_levelj<R, 1>, grid, sm, s, in, out, gt_old, gt_new, rcoarse, N, M, L, coarsest, ws, sc,
                        partials);
