@@ -24,6 +24,7 @@ Single cases for profiling (no JSON contract line):
   python bench.py --case batch [--batch 16] [--iters 100]
   python bench.py --case backward --N 256 --L 32 --iters 20
   python bench.py --case xstep --N 1024 --L 64
+  python bench.py --case configs        (64x64x8 FP64/FP32 and 256x256x32 FP32 in full, with the oracle)
 """
 
 from __future__ import annotations
@@ -161,7 +162,8 @@ def measured_peak():
 
 PAPER_SAMPLE = dict(N=256, L=15, n_sources=40, n_antennas=256, seed=15)
 PAPER_SAMPLE_NAME = "256x256x15 cube from the same recipe (seed 15, 40 sources, 256 antennas), the paper's Section 4 settings"
-ORACLE_SAMPLES = {"256x256x64": (SAMPLE, "WORKLOAD_PARAMS"), "256x256x15-paper": (PAPER_SAMPLE, "PAPER_PARAMS")}
+ORACLE_SAMPLES = {"256x256x64": (SAMPLE, "WORKLOAD_PARAMS"), "256x256x15-paper": (PAPER_SAMPLE, "PAPER_PARAMS"),
+                  "64x64x8": (None, "WORKLOAD_PARAMS"), "256x256x32": (None, "WORKLOAD_PARAMS")}
 
 
 def _oracle_rate(pb, n_iter):
@@ -180,7 +182,7 @@ def oracle_case(name, n_iter):
     from paper_1504_06847_gb300 import synth
 
     kw, params = ORACLE_SAMPLES[name]
-    c = synth.make_cube(**kw)
+    c = synth.make_cube(**kw) if kw is not None else synth.workload(name)
     v, el = _oracle_rate(oracle.Problem(c.psf, c.y, getattr(synth, params)), n_iter)
     return {"value": v, "seconds": el, "iters": n_iter}
 
@@ -499,6 +501,68 @@ def xstep_reference(stream, ours_ms):
     return {"ours_ms": ours_ms, "cufft_torch_ms": cufft, "ours_over_cufft": ours_ms / cufft}
 
 
+def _oracle_one_thread(name, n_iter):
+    """The oracle on one core, in a child process (OpenMP reads its thread count at start)."""
+    try:
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--case", "oracle", "--sample", name,
+                              "--iters", str(n_iter)], env=env, capture_output=True, text=True, timeout=600)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:  # reported, not fatal
+        return {"error": str(e)[:200]}
+
+
+def measure_configs(stream):
+    """The small configurations in full: 64 x 64 x 8 (50 iterations, FP64 and FP32
+    plans) and 256 x 256 x 32 (100 iterations, FP32), each timed with CUDA events
+    after 3 warm-up iterations, X compared with the FP64 oracle's after the same
+    iterations, and the oracle timed on every core and on one."""
+    import torch
+
+    import oracle
+    import paper_1504_06847_gb300 as mf
+    from paper_1504_06847_gb300 import synth
+
+    cores = len(os.sched_getaffinity(0))
+    os.environ["OMP_NUM_THREADS"] = str(cores)
+    peak, _ = measured_peak()
+    prm = synth.WORKLOAD_PARAMS
+    out = []
+    for name, dtype, n_iter, one_iters in (("64x64x8", torch.float64, 50, 50), ("64x64x8", torch.float32, 50, None),
+                                           ("256x256x32", torch.float32, 100, 3)):
+        c = synth.workload(name)
+        V = c.y.size
+        with torch.cuda.stream(stream):
+            plan = mf.Plan(torch.tensor(c.psf, dtype=dtype, device="cuda"))
+            y = torch.tensor(c.y, dtype=dtype, device="cuda")
+            kw = dict(prm, stream=stream.cuda_stream)
+            plan.iterate(y, 3, **kw)
+            s, e = _events(torch)
+            s.record(stream)
+            plan.iterate(y, n_iter, **kw)
+            e.record(stream)
+            stream.synchronize()
+            ms = s.elapsed_time(e)
+            x = plan.x().double().cpu().numpy()
+            plan.close()
+        pb = oracle.Problem(c.psf, c.y, prm)
+        st = pb.zero_state()
+        t0 = time.perf_counter()
+        pb.iterate(st, n_iter)
+        o_s = time.perf_counter() - t0
+        err = float(np.abs(x - st["X"]).max() / np.abs(st["X"]).max())
+        esz = 8 if dtype == torch.float64 else 4
+        ach = STEP_ALG_BYTES_PER_VOXEL * esz / 4 * V * n_iter / (ms * 1e-3) / 1e9
+        row = {"workload": name, "dtype": "f64" if esz == 8 else "f32", "iters": n_iter, "ms": ms,
+               "voxel_it_per_s": V * n_iter / (ms * 1e-3), "step_alg_gbs": ach, "step_frac": ach / peak,
+               "x_max_rel_err_vs_oracle": err,
+               "oracle": {"voxel_it_per_s": V * n_iter / o_s, "cores": cores, "iters": n_iter, "seconds": o_s}}
+        if one_iters:
+            row["oracle_one_thread"] = _oracle_one_thread(name, one_iters)
+        out.append(row)
+    return out
+
+
 def run_case(args):
     """Single runs for profiling and quick checks (no contract line)."""
     import torch
@@ -516,6 +580,9 @@ def run_case(args):
         return 0
     if args.case == "backward":
         print(json.dumps(measure_forms(stream)["differentiable"]))
+        return 0
+    if args.case == "configs":
+        print(json.dumps(measure_configs(stream)))
         return 0
     c = synth.make_cube(args.N, args.L, n_sources=max(2, int(40 * (args.N / 256) ** 2)), n_antennas=128,
                         seed=args.seed)
@@ -550,7 +617,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="leave out the batched and differentiable forms")
     ap.add_argument("--precision", default="splitbf16", choices=["splitbf16", "fp32"],
                     help="DCT arithmetic of the spectral step (the cube is FP32 either way)")
-    ap.add_argument("--case", default=None, choices=["plain", "batch", "backward", "xstep", "oracle"],
+    ap.add_argument("--case", default=None, choices=["plain", "batch", "backward", "xstep", "oracle", "configs"],
                     help="a single run for profiling instead of the benchmark line")
     ap.add_argument("--N", type=int, default=1024)
     ap.add_argument("--L", type=int, default=8)
