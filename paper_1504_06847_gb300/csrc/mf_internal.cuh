@@ -144,6 +144,8 @@ struct mf_plan {
   long long tc_stall;   // MF_OPT_TEST_TC_STALL (0: off)
   void* batch_exec;     // last batch graph launched with this plan first (cudaGraphExec_t)
   cudaStream_t batch_stream;
+  unsigned long long serial;            // unique per plan created (never reused, unlike addresses)
+  std::vector<unsigned long long> batch_key;  // what batch_exec was captured for (see batch_iterate)
   // per-kernel timing
   int timing;
   long long launches[MF_K_COUNT];

@@ -10,6 +10,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -124,6 +125,8 @@ mf_status create(int N, int L, const R* psf, mf_plan** out, bool no_psf = false)
   if (sizeof(R) == 8 && L > 64) return MF_ERR_INVALID;
   mf_plan* p = new (std::nothrow) mf_plan();
   if (!p) return MF_ERR_OOM;
+  static std::atomic<unsigned long long> next_serial{1};
+  p->serial = next_serial++;
   p->N = N;
   p->L = L;
   p->dbl = sizeof(R) == 8;
@@ -576,8 +579,52 @@ mf_status iterate(mf_plan* p, const R* y, const mf_params* prm, int n_iter) {
   return MF_OK;
 }
 
+// What a captured batch graph depends on: every plan (by serial number, with
+// its options and the Gamma_T buffer it starts from: an odd n_iter swaps the
+// double buffer), every y pointer, n_iter and every parameter but the stream.
+std::vector<unsigned long long> batch_key_of(mf_plan* const* plans, const float* const* ys, int count,
+                                             const mf_params* prm, int n_iter) {
+  std::vector<unsigned long long> k;
+  auto bits = [&](double v) {
+    unsigned long long u;
+    std::memcpy(&u, &v, sizeof(u));
+    k.push_back(u);
+  };
+  k.push_back((unsigned long long)count);
+  k.push_back((unsigned long long)n_iter);
+  for (double v : {prm->mu_eps, prm->mu_s, prm->mu_nu, prm->rho_P, prm->rho_T, prm->rho_V, prm->rho_S}) bits(v);
+  for (long long v : {(long long)prm->wavelet_levels, (long long)prm->wavelet_mask, (long long)prm->precision,
+                      (long long)prm->resid_every, (long long)prm->warm_start, (long long)prm->cg_iters,
+                      (long long)prm->spectral_mask})
+    k.push_back((unsigned long long)v);
+  for (int i = 0; i < count; i++) {
+    k.push_back(plans[i]->serial);
+    k.push_back((unsigned long long)(uintptr_t)ys[i]);
+    k.push_back((unsigned long long)plans[i]->gt_cur);
+    k.push_back((unsigned long long)plans[i]->wav_tile);
+    k.push_back((unsigned long long)plans[i]->tc_stall);
+  }
+  return k;
+}
+
+// Host-side effects of run_iterations for a replayed graph: the Gamma_T buffer
+// swap of every iteration and the residual-report bookkeeping.
+void replay_effects(mf_plan* p, const mf_params* prm, int n_iter) {
+  for (int it = 0; it < n_iter; it++) {
+    const int resid = prm->resid_every > 0 && (((it + 1) % prm->resid_every) == 0 || it == n_iter - 1);
+    if (resid) {
+      p->report_pending = 1;
+      p->report.resid_iter = p->iters_done + it + 1;
+    }
+    p->gt_cur = 1 - p->gt_cur;
+  }
+}
+
 // Batched form: every plan's n_iter iterations in one CUDA graph, each cube on
-// its own branch, launched once on prm->stream.
+// its own branch, launched once on prm->stream.  A call identical to the
+// previous one with the same first plan (same plans, y pointers, n_iter,
+// parameters, options and Gamma_T buffer) relaunches that graph instead of
+// capturing and instantiating a new one.
 mf_status batch_iterate(mf_plan* const* plans, const float* const* ys, int count, const mf_params* prm,
                         int n_iter) {
   if (!plans || !ys || !prm || count < 1 || count > 1024 || n_iter < 1) return MF_ERR_INVALID;
@@ -588,16 +635,32 @@ mf_status batch_iterate(mf_plan* const* plans, const float* const* ys, int count
   }
   cudaStream_t s = (cudaStream_t)prm->stream;
   mf_plan* owner = plans[0];
-  if (owner->batch_exec) {  // the previous batch graph of this owner
+  std::vector<unsigned long long> key = batch_key_of(plans, ys, count, prm, n_iter);
+  const bool reuse = owner->batch_exec && owner->batch_stream == s && owner->batch_key == key;
+  if (owner->batch_exec && !reuse) {  // the previous batch graph of this owner
     if (cudaStreamSynchronize(owner->batch_stream) != cudaSuccess) return MF_ERR_CUDA;
     cudaGraphExecDestroy((cudaGraphExec_t)owner->batch_exec);
     owner->batch_exec = nullptr;
+    owner->batch_key.clear();
   }
   std::vector<WavSet<float>> ws(count);
   std::vector<IterScalars<float>> sc(count);
   for (int i = 0; i < count; i++) {
     mf_status st = prepare<float>(plans[i], ys[i], prm, n_iter, s, &ws[i], &sc[i]);
     if (st != MF_OK) return st;
+  }
+  if (reuse) {
+    if (cudaGraphLaunch((cudaGraphExec_t)owner->batch_exec, s) != cudaSuccess) {
+      cudaGetLastError();
+      for (int i = 0; i < count; i++) plans[i]->status = MF_ERR_CUDA;
+      return MF_ERR_CUDA;
+    }
+    for (int i = 0; i < count; i++) {
+      replay_effects(plans[i], prm, n_iter);
+      finish(plans[i], prm, n_iter);
+      plans[i]->stream = s;
+    }
+    return MF_OK;
   }
   // The graph is recorded on a private stream (the caller's may be the legacy
   // default stream, which cannot be captured) and launched on the caller's.
@@ -652,6 +715,7 @@ mf_status batch_iterate(mf_plan* const* plans, const float* const* ys, int count
   }
   owner->batch_exec = exec;
   owner->batch_stream = s;
+  owner->batch_key = key;  // taken before the capture swapped the Gamma_T buffers
   for (int i = 0; i < count; i++) {
     finish(plans[i], prm, n_iter);
     plans[i]->stream = s;

@@ -111,3 +111,27 @@ def test_autotuner_keeps_results_identical(tmp_path):
     p.set_option(mf.MF_OPT_WAV_TILE, other)
     p.iterate(y, 5, **PRM)
     assert torch.equal(p.x(), ref.x())
+
+
+@pytest.mark.parametrize("n_iter", [4, 3])
+def test_repeated_calls_relaunch_the_graph_exactly(n_iter):
+    # identical consecutive calls relaunch the captured graph (even n_iter); an odd
+    # n_iter swaps the Gamma_T double buffer, so each call captures anew: both must
+    # equal one solo run of all the iterations, bit for bit
+    shapes = [(64, 8), (32, 4), (128, 16)]
+    cubes = _cubes(shapes, seed0=31)
+    plans, ys = _plans(cubes), _ys(cubes)
+    mf.batch_iterate(plans, ys, n_iter, **PRM)
+    for _ in range(3):
+        mf.batch_iterate(plans, ys, n_iter, warm_start=1, resid_every=2, **PRM)
+    for c, p, y in zip(cubes, plans, ys):
+        solo = mf.Plan(torch.tensor(c.psf, dtype=torch.float32, device="cuda"))
+        solo.iterate(y, n_iter, **PRM)
+        for _ in range(3):
+            solo.iterate(y, n_iter, warm_start=1, resid_every=2, **PRM)
+        a, b = _gpu.gpu_state(p), _gpu.gpu_state(solo)
+        for k in a:
+            assert np.array_equal(a[k], b[k]), (c.y.shape, k)
+        ra, rb = p.report(), solo.report()
+        assert ra["iters_done"] == rb["iters_done"] == 4 * n_iter
+        assert ra["resid_iter"] == rb["resid_iter"] and ra["objective"] == rb["objective"]
