@@ -345,6 +345,19 @@ __global__ void __launch_bounds__(WNT) k_wav_levelj(const R* __restrict__ in_img
         q, partials + (((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * MF_NQ);
 }
 
+// Residual terms of one basis on one tile, per thread, in the cube's precision
+// (the block reduction takes them to FP64 across warps), returned by value so
+// that they stay in registers across the non-inlined per-basis calls.
+template <class R>
+struct LevelSums {
+  R dgt = 0, l1s = 0, bad = 0;
+  __device__ void add(const LevelSums& o) {
+    dgt += o.dgt;
+    l1s += o.l1s;
+    bad += o.bad;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // T x T output tiles (T = 64 or 32, M >= T): compile-time shapes, runs of RB
 // outputs per thread along the filter direction, odd shared-memory pitches so
@@ -463,10 +476,11 @@ cudaError_t upload_tap_pairs() {
 // thread's item s (fixed across calls); after_rows() runs once the input tile
 // has been consumed (all threads past the row analysis).
 template <class R, int T, int K, int RESID, class Emit, class AfterRows>
-__device__ __forceinline__ void level_tile_t(const R* in, int off, R* rpair, R* spair, int M, int y0, int x0,
-                                             const R* __restrict__ gto, R* __restrict__ gtn, int N,
-                                             const R* __restrict__ rco, const IterScalars<R>& sc, R w, double* q,
-                                             Emit emit, AfterRows after_rows) {
+__device__ __forceinline__ LevelSums<R> level_tile_t(const R* in, int off, R* rpair, R* spair, int M, int y0,
+                                                     int x0, const R* __restrict__ gto, R* __restrict__ gtn, int N,
+                                                     const R* __restrict__ rco, const IterScalars<R>& sc, R w,
+                                                     Emit emit, AfterRows after_rows) {
+  LevelSums<R> sums;
   typedef TC<T> C;
   typedef typename V2<R>::T P;
   constexpr int F = 2 * K;
@@ -594,9 +608,9 @@ __device__ __forceinline__ void level_tile_t(const R* in, int off, R* rpair, R* 
         bot[row * B_CP + c] = mk2(update(hi.x, gbl[i], own, go[i] + MhN), update(hi.y, gbr[i], own, go[i] + MhN + Mh));
       }
       if (RESID == 1) {
-        q[Q_DGT] += (double)w * (double)r_dg;
-        q[Q_L1S] += (double)w * (double)r_l1;
-        if (r_bad) q[Q_NONFIN] += 1.0;
+        sums.dgt = fma(w, r_dg, sums.dgt);
+        sums.l1s = fma(w, r_l1, sums.l1s);
+        if (r_bad) sums.bad += (R)1;
       }
     }
   }
@@ -661,6 +675,7 @@ __device__ __forceinline__ void level_tile_t(const R* in, int off, R* rpair, R* 
       emit(s, m, OPI * j, out);
     }
   }
+  return sums;
 }
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -698,16 +713,16 @@ __device__ __forceinline__ void load_tile_t(const R* __restrict__ img, int M, in
 // operands instead of having all lengths' taps hoisted into registers across
 // the loop over bases.
 template <class R, int T, int K, int RESID>
-__device__ __noinline__ void level1_basis(const R* in, R* ra, R* sb, R* bacc, int N, int y0, int x0,
-                                          const R* __restrict__ gto, R* __restrict__ gtn, const R* __restrict__ rco,
-                                          IterScalars<R> sc, R w, double* q) {
+__device__ __noinline__ LevelSums<R> level1_basis(const R* in, R* ra, R* sb, R* bacc, int N, int y0, int x0,
+                                                  const R* __restrict__ gto, R* __restrict__ gtn,
+                                                  const R* __restrict__ rco, IterScalars<R> sc, R w) {
   auto emit = [&](int, int m, int x, const R* v) {
     R* a = bacc + m * TC<T>::BP + x;
 #pragma unroll
     for (int t = 0; t < TC<T>::OPI; t++) a[t] = fma(w, v[t], a[t]);
   };
-  level_tile_t<R, T, K, RESID>(in, 2 * (MF_MAX_K - K), ra, sb, N, y0, x0, gto, gtn, N, rco, sc, w, q, emit,
-                               [] {});
+  return level_tile_t<R, T, K, RESID>(in, 2 * (MF_MAX_K - K), ra, sb, N, y0, x0, gto, gtn, N, rco, sc, w, emit,
+                                      [] {});
 }
 
 template <class R, int T, int RESID>
@@ -731,10 +746,7 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_level1_t(const R* __re
   if (ws->nd > 0)
     prefetch_level<R, T>(ws->K[0], gto + (size_t)band * NN, coarsest ? nullptr : rco + (size_t)band * (NN / 4), N,
                          N, y0, x0);
-  double q[Q_COUNT];
-#pragma unroll
-  for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
-  q[Q_XMIN] = 1e300;
+  LevelSums<R> tot;
   // the weighted sum over bases accumulates in shared memory; each thread owns
   // the same outputs for every basis
   R* bacc = sb + 4 * C::SBQ;
@@ -751,8 +763,8 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_level1_t(const R* __re
                            coarsest ? nullptr : rco + ((size_t)(k + 1) * L + band) * (NN / 4), N, N, y0, x0);
       if (RESID == 2) prefetch_level<R, T>(ws->K[k + 1], gtn + g1, nullptr, N, N, y0, x0);
     }
-    MF_K_SWITCH(ws->K[k], (level1_basis<R, T, KK, RESID>(in, ra, sb, bacc, N, y0, x0, gto + gofs, gtn + gofs,
-                                                         rc, sc, w, q)));
+    MF_K_SWITCH(ws->K[k], (tot.add(level1_basis<R, T, KK, RESID>(in, ra, sb, bacc, N, y0, x0, gto + gofs,
+                                                                 gtn + gofs, rc, sc, w))));
     __syncthreads();
   }
   for (int e = threadIdx.x; e < T * T; e += WNT) {
@@ -763,7 +775,11 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_level1_t(const R* __re
   if (RESID == 1) {
     R qr[Q_COUNT];  // FP32 plans take the FP32 warp stage of the reduction
 #pragma unroll
-    for (int i = 0; i < Q_COUNT; i++) qr[i] = (R)q[i];
+    for (int i = 0; i < Q_COUNT; i++) qr[i] = 0;
+    qr[Q_XMIN] = NoMin<R>::v;
+    qr[Q_DGT] = tot.dgt;
+    qr[Q_L1S] = tot.l1s;
+    qr[Q_NONFIN] = tot.bad;
     block_reduce_write<WNT>(qr, partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * MF_NQ);
   }
 }
@@ -774,10 +790,10 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_level1_t(const R* __re
 // half-length next_K; none when next_src is null).  Not inlined (see
 // level1_basis).
 template <class R, int T, int K, int RESID>
-__device__ __noinline__ void levelj_basis(R* in, R* ra, R* sb, R* __restrict__ dst, int M, int y0, int x0,
-                                          const R* __restrict__ gto, R* __restrict__ gtn, int N,
-                                          const R* __restrict__ rco, IterScalars<R> sc, R w, double* q,
-                                          const R* __restrict__ next_src, int next_K) {
+__device__ __noinline__ LevelSums<R> levelj_basis(R* in, R* ra, R* sb, R* __restrict__ dst, int M, int y0, int x0,
+                                                  const R* __restrict__ gto, R* __restrict__ gtn, int N,
+                                                  const R* __restrict__ rco, IterScalars<R> sc, R w,
+                                                  const R* __restrict__ next_src, int next_K) {
   auto emit = [&](int, int m, int x, const R* v) {
     R* o = dst + (size_t)(y0 + m) * M + x0 + x;
 #pragma unroll
@@ -787,7 +803,7 @@ __device__ __noinline__ void levelj_basis(R* in, R* ra, R* sb, R* __restrict__ d
     if (next_src != nullptr)
       load_tile_t<R, T>(next_src, M, y0 - 2 * next_K + 2, x0 - 2 * next_K + 2, T + 4 * next_K - 4, in);
   };
-  level_tile_t<R, T, K, RESID>(in, 0, ra, sb, M, y0, x0, gto, gtn, N, rco, sc, w, q, emit, after_rows);
+  return level_tile_t<R, T, K, RESID>(in, 0, ra, sb, M, y0, x0, gto, gtn, N, rco, sc, w, emit, after_rows);
 }
 
 // L2 prefetch of a basis's input tile at a coarser level.
@@ -818,10 +834,7 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_levelj_t(const R* __re
   const int band = blockIdx.y;
   const int y0 = (blockIdx.x / tpd) * T, x0 = (blockIdx.x % tpd) * T;
   const size_t MM = (size_t)M * M, NN = (size_t)N * N;
-  double q[Q_COUNT];
-#pragma unroll
-  for (int i = 0; i < Q_COUNT; i++) q[i] = 0.0;
-  q[Q_XMIN] = 1e300;
+  LevelSums<R> tot;
   // this CTA's bases: group blockIdx.z of gridDim.z equal groups
   const int per = (ws->nd + gridDim.z - 1) / gridDim.z;
   const int kb = blockIdx.z * per;
@@ -846,15 +859,20 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_levelj_t(const R* __re
     __syncthreads();
     const size_t gofs = ((size_t)k * L + band) * NN;
     R* dst = out_img + ((size_t)k * L + band) * MM;
-    MF_K_SWITCH(ws->K[k], (levelj_basis<R, T, KK, RESID>(in, ra, sb, dst, M, y0, x0, gto + gofs, gtn + gofs, N,
-                                                         rc_of(k), sc, ws->w[k], q, more ? src_of(k + 1) : nullptr,
-                                                         more ? ws->K[k + 1] : 0)));
+    MF_K_SWITCH(ws->K[k], (tot.add(levelj_basis<R, T, KK, RESID>(in, ra, sb, dst, M, y0, x0, gto + gofs,
+                                                                 gtn + gofs, N, rc_of(k), sc, ws->w[k],
+                                                                 more ? src_of(k + 1) : nullptr,
+                                                                 more ? ws->K[k + 1] : 0))));
     __syncthreads();
   }
   if (RESID == 1) {
     R qr[Q_COUNT];  // FP32 plans take the FP32 warp stage of the reduction
 #pragma unroll
-    for (int i = 0; i < Q_COUNT; i++) qr[i] = (R)q[i];
+    for (int i = 0; i < Q_COUNT; i++) qr[i] = 0;
+    qr[Q_XMIN] = NoMin<R>::v;
+    qr[Q_DGT] = tot.dgt;
+    qr[Q_L1S] = tot.l1s;
+    qr[Q_NONFIN] = tot.bad;
     block_reduce_write<WNT>(
         qr, partials + (((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * MF_NQ);
   }
