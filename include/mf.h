@@ -205,8 +205,8 @@ typedef enum {
 } mf_array;
 
 /* Device-to-device copies of a state array (dst/src: device, plan's real
- * type).  *count receives the element count when dst is NULL.  These calls
- * synchronise the plan's last stream. */
+ * type).  *count receives the element count when dst is NULL.  The copy runs
+ * on the plan's last stream after its work and is complete on return. */
 mf_status mf_plan_get_array(mf_plan* p, int which, void* dst, size_t* count);
 mf_status mf_plan_set_array(mf_plan* p, int which, const void* src, size_t count);
 

@@ -889,6 +889,14 @@ mf_status mf_batch_iterate(mf_plan* const* plans, const float* const* y_cubes, i
   return batch_iterate(plans, y_cubes, count, prm, n_iter);
 }
 
+// Device-to-device copy on the plan's stream, complete on return (a plain
+// cudaMemcpy between device buffers may return before the copy has finished,
+// and the legacy stream it uses is not ordered with non-blocking streams).
+static bool copy_d2d(mf_plan* p, void* dst, const void* src, size_t bytes) {
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, p->stream) == cudaSuccess &&
+         cudaStreamSynchronize(p->stream) == cudaSuccess;
+}
+
 mf_status mf_plan_get_array(mf_plan* p, int which, void* dst, size_t* count) {
   if (!p) return MF_ERR_INVALID;
   size_t n = 0;
@@ -897,7 +905,7 @@ mf_status mf_plan_get_array(mf_plan* p, int which, void* dst, size_t* count) {
   if (count) *count = n;
   if (!dst) return count ? MF_OK : MF_ERR_INVALID;
   if (cudaStreamSynchronize(p->stream) != cudaSuccess) return MF_ERR_CUDA;
-  if (cudaMemcpy(dst, src, n * p->esz, cudaMemcpyDeviceToDevice) != cudaSuccess) return MF_ERR_CUDA;
+  if (!copy_d2d(p, dst, src, n * p->esz)) return MF_ERR_CUDA;
   return MF_OK;
 }
 
@@ -908,7 +916,7 @@ mf_status mf_plan_set_array(mf_plan* p, int which, const void* src, size_t count
   if (which == MF_ARR_GAMMA_T) n = p->cube * MF_MAX_BASES;
   if (!dst || count > n || (which != MF_ARR_GAMMA_T && count != n)) return MF_ERR_INVALID;
   if (cudaStreamSynchronize(p->stream) != cudaSuccess) return MF_ERR_CUDA;
-  if (cudaMemcpy(dst, src, count * p->esz, cudaMemcpyDeviceToDevice) != cudaSuccess) return MF_ERR_CUDA;
+  if (!copy_d2d(p, dst, src, count * p->esz)) return MF_ERR_CUDA;
   if (which == MF_ARR_GAMMA_T) p->nd_state = (int)(count / p->cube);
   return MF_OK;
 }
@@ -926,11 +934,10 @@ mf_status mf_plan_get_state(mf_plan* p, void* buf, size_t* bytes) {
   void* src[] = {p->X, p->b, p->GP, p->Sd, p->GV, p->GV2, p->GSd};
   char* d = (char*)buf;
   for (void* s : src) {
-    if (cudaMemcpy(d, s, cb, cudaMemcpyDeviceToDevice) != cudaSuccess) return MF_ERR_CUDA;
+    if (!copy_d2d(p, d, s, cb)) return MF_ERR_CUDA;
     d += cb;
   }
-  if (cudaMemcpy(d, p->GT[p->gt_cur], cb * MF_MAX_BASES, cudaMemcpyDeviceToDevice) != cudaSuccess)
-    return MF_ERR_CUDA;
+  if (!copy_d2d(p, d, p->GT[p->gt_cur], cb * MF_MAX_BASES)) return MF_ERR_CUDA;
   return MF_OK;
 }
 
@@ -942,11 +949,10 @@ mf_status mf_plan_set_state(mf_plan* p, const void* buf, size_t bytes) {
   void* dst[] = {p->X, p->b, p->GP, p->Sd, p->GV, p->GV2, p->GSd};
   const char* s = (const char*)buf;
   for (void* d : dst) {
-    if (cudaMemcpy(d, s, cb, cudaMemcpyDeviceToDevice) != cudaSuccess) return MF_ERR_CUDA;
+    if (!copy_d2d(p, d, s, cb)) return MF_ERR_CUDA;
     s += cb;
   }
-  if (cudaMemcpy(p->GT[p->gt_cur], s, cb * MF_MAX_BASES, cudaMemcpyDeviceToDevice) != cudaSuccess)
-    return MF_ERR_CUDA;
+  if (!copy_d2d(p, p->GT[p->gt_cur], s, cb * MF_MAX_BASES)) return MF_ERR_CUDA;
   if (p->iters_done == 0) p->iters_done = 1;
   return MF_OK;
 }
