@@ -21,6 +21,7 @@ cores instead, one Algorithm-1 iteration of the workload per step.
 
 Single cases for profiling (no JSON contract line):
   python bench.py --case plain --N 1024 --L 8 --iters 2 [--precision fp32|splitbf16] [--tile 64|32] [--resid]
+                   [--spectral-mask 1|2|3]
   python bench.py --case batch [--batch 16] [--iters 100]
   python bench.py --case backward --N 256 --L 32 --iters 20
   python bench.py --case xstep --N 1024 --L 64
@@ -611,7 +612,7 @@ def run_case(args):
             print(json.dumps(dict(xstep_reference(stream, ours), N=args.N, L=args.L)))
             return 0
         plan.iterate(y, args.iters, wavelet_levels=args.J, precision=prec, resid_every=1 if args.resid else 0,
-                     **prm)
+                     spectral_mask=args.spectral_mask, **prm)
         print(json.dumps(plan.report()))
     return 0
 
@@ -634,6 +635,8 @@ def main():
     ap.add_argument("--iters", type=int, default=2)
     ap.add_argument("--tile", type=int, default=64, choices=[64, 32])
     ap.add_argument("--resid", action="store_true")
+    ap.add_argument("--spectral-mask", type=int, default=1, choices=[1, 2, 3],
+                    help="spectral dictionary of --case plain: 1 DCT, 2 Chebyshev, 3 both (FP32 DCT)")
     ap.add_argument("--seed", type=int, default=9)
     ap.add_argument("--sample", default="256x256x64", choices=sorted(ORACLE_SAMPLES))
     args = ap.parse_args()

@@ -248,6 +248,17 @@ __global__ void __launch_bounds__(SP_NT) k_spectral_b2(const R* __restrict__ X, 
       V4<R>::st(T + l * PT + p, v);
     }
   };
+  {
+    // L2 prefetch of the tile's rows of the state arrays read after the first
+    // products (S, Gamma_V2, Gamma_V, Gamma_S, Gamma_P): one per 128-byte line
+    constexpr int LINES = (PT * (int)sizeof(R) + 127) / 128;
+    const R* arr[5] = {Sd, GV2, GSd, GP, DCT_ON ? GV : Sd};
+    for (int e = tid; e < (DCT_ON ? 5 : 4) * L * LINES; e += SP_NT) {
+      const int a = e / (L * LINES), r = e % (L * LINES);
+      const int l = r / LINES, ln = r % LINES;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(arr[a] + (size_t)l * NN + p0 + ln * (128 / (int)sizeof(R))));
+    }
+  }
   // out[a][c] = sum_l A[kb + a][l] T[l][pb + c], with AT = A transposed in shared memory
   auto product = [&](const R* AT, R (&out)[4][4], int kb, int pb) {
 #pragma unroll
