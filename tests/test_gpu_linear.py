@@ -74,3 +74,13 @@ def test_linear_plan_rejects_bad_use():
     assert e.value.status == mf.MF_ERR_INVALID
     with pytest.raises(ValueError):
         mf.Plan(torch.tensor(c.psf, dtype=torch.float64, device="cuda"), linear=True)
+
+
+def test_largest_image():
+    # N = 1024, the largest a linear-convolution plan takes (its transforms run at 2N = 2048)
+    c = synth.make_cube(1024, 2, n_sources=6, n_antennas=40, seed=96)
+    pb = oracle.Problem(c.psf, c.y, PRM, conv="linear", cg_iters=2)
+    st, _ = pb.run(1)
+    plan = _run(c, 1, 2)
+    errs = _gpu.compare(_gpu.gpu_state(plan), _gpu.oracle_view(pb, st), _gpu.scales(pb, st))
+    assert max(errs.values()) < 1e-5, errs

@@ -99,3 +99,16 @@ def test_dictionary_rejections(gpu):
         assert e.value.status == mf.MF_ERR_INVALID
     with pytest.raises(mf.MFError):
         plan.backward(y, 2, torch.zeros_like(y), rho=1.0, spectral_mask=3)
+
+
+@pytest.mark.gpu
+def test_most_bands(gpu):
+    # L = 64, the most bands the Chebyshev basis is offered for
+    c = synth.make_cube(32, 64, n_sources=3, n_antennas=16, seed=98)
+    pb = oracle.Problem(c.psf, c.y, PRM, spectral=("dct", "cheb"))
+    st, _ = pb.run(8)
+    plan = mf.Plan(torch.tensor(c.psf, dtype=torch.float32, device="cuda"))
+    plan.iterate(torch.tensor(c.y, dtype=torch.float32, device="cuda"), 8, spectral_mask=3, **PRM)
+    g, o, sc = _views(plan, pb, st, 3)
+    errs = _gpu.compare(g, o, sc, keys=tuple(g))
+    assert max(errs.values()) < 1e-5, errs

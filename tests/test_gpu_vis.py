@@ -153,3 +153,39 @@ def test_unit_weights_without_a_weight_array():
     assert _gpu.rel_err(plan.get(mf.ARR_HTY).double().cpu().numpy(), pb.HtY) < 1e-5
     errs = _gpu.compare(_gpu.gpu_state(plan), _gpu.oracle_view(pb, st), _gpu.scales(pb, st))
     assert max(errs.values()) < 1e-5, errs
+
+
+def test_largest_image():
+    # N = 512, the largest a visibility plan takes (its Toeplitz kernels are gridded at 4N)
+    c = synth.make_visibilities(512, 2, n_sources=8, n_antennas=20, seed=95, random_weights=True)
+    pb = _problem(512, c, 3)
+    st, _ = pb.run(2)
+    plan = _plan(512, c)
+    plan.iterate(_y(c), 2, cg_iters=3, **PRM)
+    errs = {"HtY": _gpu.rel_err(plan.get(mf.ARR_HTY).double().cpu().numpy(), pb.HtY)}
+    errs.update(_gpu.compare(_gpu.gpu_state(plan), _gpu.oracle_view(pb, st), _gpu.scales(pb, st)))
+    assert max(errs.values()) < 1e-5, errs
+
+
+def test_all_visibilities_at_the_origin():
+    # degenerate coverage: every uv point at (0, 0), so k is the constant sum of the
+    # weights and Re(Phi^H W Phi) = (sum w) 1 1^T has rank one, with the eigenvalue
+    # N^2 sum w.  The weights are scaled to sum 1/N^2 so that this eigenvalue is 1 and
+    # Q stays well conditioned (with sum w = 1 its condition number is about 94 at
+    # N = 32 and FP32 conjugate gradients drift about 6e-5 from the FP64 ones)
+    c = synth.make_visibilities(32, 3, n_sources=2, n_antennas=8, seed=97, random_weights=True)
+    # one ADMM iteration: with such weak data the regularisers shrink X about 70-fold
+    # by the third, which leaves X a small difference of right-hand-side terms (its
+    # relative error there, ~3e-5, is the FP32 rounding of those terms, ~3e-10)
+    c.uv = [np.zeros_like(q) for q in c.uv]
+    c.weights = [a / 32 ** 2 for a in c.weights]
+    pb = _problem(32, c, 4)
+    st, _ = pb.run(1)
+    plan = _plan(32, c)
+    plan.iterate(_y(c), 1, cg_iters=4, **PRM)
+    d = plan.get(mf.ARR_HTY).double().cpu().numpy()
+    errs = {"HtY": _gpu.rel_err(d, pb.HtY)}
+    errs.update(_gpu.compare(_gpu.gpu_state(plan), _gpu.oracle_view(pb, st), _gpu.scales(pb, st)))
+    assert max(errs.values()) < 1e-5, errs
+    for l in range(3):  # the dirty image of band l is the constant Re(sum_m w_m y_m)
+        assert np.ptp(d[l]) <= 1e-5 * np.abs(d[l]).max()
