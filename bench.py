@@ -374,13 +374,13 @@ def measure_forms(stream, xstep_ms=None):
 
 
 # Bytes per voxel of the N x N cube moved by one conjugate-gradient iteration of
-# step I (FP32; the 2N x 2N images hold 4 values per voxel).  One 2N
-# convolution: row transform 16 in + 16 out, column pass (spectrum in and out,
-# transfer function in) 48, inverse rows 16 + 16: 112.  Zero padding writes 16
-# (reads 4); the crop-and-pad of the linear operator reads and writes 32.  The
-# CG vector updates (q, X and r, p) move 48.  Linear convolution: two
-# convolutions per operator application; visibilities: one.
-CG_BYTES = {"linear": 20 + 112 + 32 + 112 + 48, "vis": 20 + 112 + 48}
+# step I (FP32).  One zero-padded 2N convolution with its known zeros and
+# discarded outputs skipped: row transform 4 in (the N x N image) + 8 out (the
+# first N rows' half spectra), column pass 8 in + 16 (the 2N x N complex
+# transfer function) + 8 out (first N rows), inverse rows 8 in + 4 out
+# ([0,N)^2): 56.  The CG vector updates (q; X and r; p) move 48.  Linear
+# convolution: two convolutions per operator application; visibilities: one.
+CG_BYTES = {"linear": 2 * 56 + 48, "vis": 56 + 48}
 # the spectral step with the Chebyshev basis added: X in; Gamma_P, S, Gamma_V,
 # Gamma_V2, Gamma_S in and out; b out
 SPECTRAL_B2_BYTES = 4 + 5 * 8 + 4

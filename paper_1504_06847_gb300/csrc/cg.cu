@@ -12,8 +12,10 @@
 // image at [0,N)^2, the PSF at offsets (u - N/2) mod 2N, and the circular
 // convolution of size 2N -- the plan's own FFT kernels at 2N -- has no
 // wrap-around on the [0,N)^2 output.  Q p = crop(H^T pad(crop(H pad(p)))) +
-// rho p: pad, forward row FFT, column FFT with h (MODE 3), inverse, zero
-// outside [0,N)^2, forward, column FFT with conj(h) (MODE 5), inverse.
+// rho p.  The transforms skip the known zeros and the discarded outputs: the
+// row pass reads the N x N image as the padded one, the column pass works on
+// the first N spatial rows only, the inverse row pass writes only [0,N)^2
+// (conv2n), so pad and crop cost no pass of their own.
 //
 // Per-band dot products: each band's elements are summed by MF_CG_CHUNKS
 // blocks in the cube's precision per thread and FP64 across threads and
@@ -38,38 +40,6 @@ unsigned grid_of(size_t n) {
   return (unsigned)(b < 152 * 16 ? (b ? b : 1) : 152 * 16);
 }
 
-// dst [L][2N][2N] = src [L][N][N] at [0,N)^2, zero elsewhere
-__global__ void k_pad(const float* __restrict__ src, float* __restrict__ dst, int N, int L) {
-  const int M = 2 * N;
-  const size_t MM = (size_t)M * M, total = MM * L;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t l = i / MM, rem = i - l * MM;
-    const int r = (int)(rem / M), c = (int)(rem - (size_t)r * M);
-    dst[i] = (r < N && c < N) ? src[(l * N + r) * N + c] : 0.f;
-  }
-}
-
-// in place: zero every pixel of the 2N x 2N images outside [0,N)^2 (crop, then pad)
-__global__ void k_crop_pad(float* __restrict__ img, int N, int L) {
-  const int M = 2 * N;
-  const size_t MM = (size_t)M * M, total = MM * L;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t rem = i % MM;
-    const int r = (int)(rem / M), c = (int)(rem - (size_t)r * M);
-    if (r >= N || c >= N) img[i] = 0.f;
-  }
-}
-
-// dst [L][N][N] = the [0,N)^2 region of src [L][2N][2N]
-__global__ void k_crop(const float* __restrict__ src, float* __restrict__ dst, int N, int L) {
-  const size_t NN = (size_t)N * N, total = NN * L;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t l = i / NN, rem = i - l * NN;
-    const int r = (int)(rem / N), c = (int)(rem - (size_t)r * N);
-    dst[i] = src[((l * 2 * N) + r) * 2 * N + c];
-  }
-}
-
 // the PSF of band l at offsets (u - N/2) mod 2N of a 2N x 2N image
 __global__ void k_embed_psf(const float* __restrict__ psf, float* __restrict__ dst, int N, int L) {
   const int M = 2 * N;
@@ -90,9 +60,6 @@ __global__ void k_embed_psf(const float* __restrict__ psf, float* __restrict__ d
     const size_t NN = (size_t)(N) * (N);                                                     \
     for (size_t e = blockIdx.x * (size_t)CNT + threadIdx.x; e < NN; e += (size_t)CNT * gridDim.x) { \
       const size_t o = l * NN + e;                                                           \
-      const int row = (int)(e / (N)), col = (int)(e - (size_t)row * (N));                   \
-      const size_t ob = ((size_t)l * 2 * (N) + row) * 2 * (N) + col;                         \
-      (void)ob;                                                                              \
       body                                                                                   \
     }                                                                                        \
   }
@@ -110,14 +77,14 @@ __device__ __forceinline__ void band_partial(float v, double* part) {
   }
 }
 
-// r = (H^T y + b) - (t + rho X), p = r, with t = H^T H X in big; partial r.r
-__global__ void __launch_bounds__(CNT) k_cg_init(const float* __restrict__ big, const float* __restrict__ hty,
+// r = (H^T y + b) - (t + rho X), p = r, with t = H^T H X; partial r.r
+__global__ void __launch_bounds__(CNT) k_cg_init(const float* __restrict__ t, const float* __restrict__ hty,
                                                  const float* __restrict__ b, const float* __restrict__ X,
                                                  float* __restrict__ r, float* __restrict__ p, int N, float rho,
                                                  double* __restrict__ part) {
   float s = 0.f;
   CG_BAND_LOOP(N, {
-    const float v = (hty[o] + b[o]) - (big[ob] + rho * X[o]);
+    const float v = (hty[o] + b[o]) - (t[o] + rho * X[o]);
     r[o] = v;
     p[o] = v;
     s = fmaf(v, v, s);
@@ -125,12 +92,12 @@ __global__ void __launch_bounds__(CNT) k_cg_init(const float* __restrict__ big, 
   band_partial(s, part);
 }
 
-// q = t + rho p, t = H^T H p in big; partial p.q
-__global__ void __launch_bounds__(CNT) k_cg_q(const float* __restrict__ big, const float* __restrict__ p,
+// q = t + rho p, t = H^T H p; partial p.q
+__global__ void __launch_bounds__(CNT) k_cg_q(const float* __restrict__ t, const float* __restrict__ p,
                                               float* __restrict__ q, int N, float rho, double* __restrict__ part) {
   float s = 0.f;
   CG_BAND_LOOP(N, {
-    const float v = big[ob] + rho * p[o];
+    const float v = t[o] + rho * p[o];
     q[o] = v;
     s = fmaf(p[o], v, s);
   });
@@ -201,12 +168,12 @@ __global__ void k_cg_scalars(const double* __restrict__ part, int chunks, double
   }
 }
 
-// 1/2 (y - H X)^2 partials into the Q_FIT slot, H X in big
-__global__ void __launch_bounds__(CNT) k_cg_fit(const float* __restrict__ big, const float* __restrict__ y, int N,
+// 1/2 (y - H X)^2 partials into the Q_FIT slot, t = H X
+__global__ void __launch_bounds__(CNT) k_cg_fit(const float* __restrict__ t, const float* __restrict__ y, int N,
                                                 double* __restrict__ partials) {
   float s = 0.f;
   CG_BAND_LOOP(N, {
-    const float d = y[o] - big[ob];
+    const float d = y[o] - t[o];
     s = fmaf(d, d, s);
   });
   float q[Q_COUNT];
@@ -217,30 +184,27 @@ __global__ void __launch_bounds__(CNT) k_cg_fit(const float* __restrict__ big, c
   block_reduce_write<CNT>(q, partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * MF_NQ);
 }
 
-// big <- conv(big) through the 2N FFT kernels: mode 3 (H) or 5 (H^T)
-cudaError_t conv2n(mf_plan* p, int mode, cudaStream_t s) {
-  const int M = 2 * p->N, L = p->L;
-  cudaError_t e = launch_rows_fwd<float>((const float*)p->big, (C*)p->work2, M, M * L, (const C*)p->tw2, s);
-  if (!e)
-    e = launch_cols<float>((C*)p->work2, M, L, (const C*)p->tw2, mode, nullptr, nullptr, nullptr, nullptr, nullptr,
-                           nullptr, (const C*)p->h2, (const C*)p->h2_nyq, nullptr, nullptr, nullptr, s);
-  if (!e) e = launch_rows_inv<float>((const C*)p->work2, (float*)p->big, M, M * L, (const C*)p->tw2, s);
+// dst [L][N][N] = [0,N)^2 region of the circular 2N convolution of src [L][N][N]
+// (zero-padded) by the band's transfer function h2: mode 3 (H, or the
+// Toeplitz kernel of a visibility plan) or 5 (H^T)
+cudaError_t conv2n(mf_plan* p, const float* src, float* dst, int mode, cudaStream_t s) {
+  const int M = 2 * p->N, rows = p->N * p->L;
+  cudaError_t e = launch_rows_fwd_pad(src, (C*)p->work2, M, rows, (const C*)p->tw2, s);
+  if (!e) e = launch_cols_pruned((C*)p->work2, M, p->L, (const C*)p->tw2, mode, (const C*)p->h2, (const C*)p->h2_nyq, s);
+  if (!e) e = launch_rows_inv_crop((const C*)p->work2, dst, M, rows, (const C*)p->tw2, s);
   return e;
 }
 
-// big <- H^T crop(H pad(src)) (2N x 2N; the caller reads its [0,N)^2 region).
-// Visibility plans: big <- kr * pad(src), the Toeplitz form of Re(Phi^H W Phi) (vis.cu).
+// the operator's output cube (the first cube of big; the second is the linear
+// operator's intermediate H src)
+float* op_out(mf_plan* p) { return (float*)p->big; }
+
+// op_out <- H^T H src (linear convolution) or Re(Phi^H W Phi) src (visibilities, vis.cu)
 cudaError_t apply_hth(mf_plan* p, const float* src, cudaStream_t s) {
-  const size_t big_n = (size_t)4 * p->cube;
-  k_pad<<<grid_of(big_n), CNT, 0, s>>>(src, (float*)p->big, p->N, p->L);
-  cudaError_t e = cudaGetLastError();
-  if (!e) e = conv2n(p, 3, s);
-  if (p->vis) return e;
-  if (!e) {
-    k_crop_pad<<<grid_of(big_n), CNT, 0, s>>>((float*)p->big, p->N, p->L);
-    e = cudaGetLastError();
-  }
-  if (!e) e = conv2n(p, 5, s);
+  if (p->vis) return conv2n(p, src, op_out(p), 3, s);
+  float* mid = op_out(p) + p->cube;
+  cudaError_t e = conv2n(p, src, mid, 3, s);
+  if (!e) e = conv2n(p, mid, op_out(p), 5, s);
   return e;
 }
 
@@ -268,15 +232,7 @@ cudaError_t linear_setup(mf_plan* p, const float* psf) {
 
 cudaError_t linear_hty(mf_plan* p, const float* y, cudaStream_t s) {
   if (p->vis) return vis_dirty(p, y, s);
-  const size_t big_n = (size_t)4 * p->cube;
-  k_pad<<<grid_of(big_n), CNT, 0, s>>>(y, (float*)p->big, p->N, p->L);
-  cudaError_t e = cudaGetLastError();
-  if (!e) e = conv2n(p, 5, s);
-  if (!e) {
-    k_crop<<<grid_of(p->cube), CNT, 0, s>>>((const float*)p->big, (float*)p->cgv, p->N, p->L);  // H^T y
-    e = cudaGetLastError();
-  }
-  return e;
+  return conv2n(p, y, (float*)p->cgv, 5, s);  // H^T y
 }
 
 cudaError_t linear_step_I(mf_plan* p, int cg_iters, double rho_bar, cudaStream_t s) {
@@ -291,14 +247,14 @@ cudaError_t linear_step_I(mf_plan* p, int cg_iters, double rho_bar, cudaStream_t
   const float rho = (float)rho_bar;
   cudaError_t e = apply_hth(p, X, s);
   if (!e) {
-    k_cg_init<<<g, CNT, 0, s>>>((const float*)p->big, hty, (const float*)p->b, X, r, pv, N, rho, p->cgpart);
+    k_cg_init<<<g, CNT, 0, s>>>(op_out(p), hty, (const float*)p->b, X, r, pv, N, rho, p->cgpart);
     k_cg_scalars<<<1, 128, 0, s>>>(p->cgpart, MF_CG_CHUNKS, p->cgs, L, 0);
     e = cudaGetLastError();
   }
   for (int it = 0; it < cg_iters && !e; it++) {
     e = apply_hth(p, pv, s);
     if (e) break;
-    k_cg_q<<<g, CNT, 0, s>>>((const float*)p->big, pv, q, N, rho, p->cgpart);
+    k_cg_q<<<g, CNT, 0, s>>>(op_out(p), pv, q, N, rho, p->cgpart);
     k_cg_scalars<<<1, 128, 0, s>>>(p->cgpart, MF_CG_CHUNKS, p->cgs, L, 1);
     k_cg_step<<<g, CNT, 0, s>>>(X, r, pv, q, p->cgs, N, L, p->cgpart);
     k_cg_scalars<<<1, 128, 0, s>>>(p->cgpart, MF_CG_CHUNKS, p->cgs, L, 2);
@@ -309,14 +265,11 @@ cudaError_t linear_step_I(mf_plan* p, int cg_iters, double rho_bar, cudaStream_t
 }
 
 cudaError_t linear_fit(mf_plan* p, const float* y, double* partials, int* nblocks, cudaStream_t s) {
-  const size_t big_n = (size_t)4 * p->cube;
-  k_pad<<<grid_of(big_n), CNT, 0, s>>>((const float*)p->X, (float*)p->big, p->N, p->L);
-  cudaError_t e = cudaGetLastError();
-  if (!e) e = conv2n(p, 3, s);
+  cudaError_t e = conv2n(p, (const float*)p->X, op_out(p), 3, s);  // H X (or A X for visibilities)
   if (e) return e;
-  if (p->vis) return vis_fit(p, partials, nblocks, s);
+  if (p->vis) return vis_fit(p, op_out(p), partials, nblocks, s);
   const dim3 g(MF_CG_CHUNKS, p->L);
-  k_cg_fit<<<g, CNT, 0, s>>>((const float*)p->big, y, p->N, partials);
+  k_cg_fit<<<g, CNT, 0, s>>>(op_out(p), y, p->N, partials);
   *nblocks = MF_CG_CHUNKS * p->L;
   return cudaGetLastError();
 }

@@ -165,7 +165,10 @@ template <class R, int N> struct ColCfg {
 // ---------------------------------------------------------------------------
 // rows_fwd: real rows of length N -> packed half spectrum rows (N/2 complex).
 // ---------------------------------------------------------------------------
-template <class R, int N>
+// PADIN: the rows are those of an N/2 x N/2 image per band, zero-padded to
+// N x N (input pitch N/2, upper half of each row zero; rows = (N/2) L); output
+// row r of band l goes to row l N + r (rows N/2..N-1 of each band are not written).
+template <class R, int N, bool PADIN = false>
 __global__ void __launch_bounds__(FFT_NT) k_rows_fwd(const R* __restrict__ in, cx<R>* __restrict__ out,
                                                      int rows, const cx<R>* __restrict__ tw) {
   constexpr int n = N / 2;
@@ -177,7 +180,8 @@ __global__ void __launch_bounds__(FFT_NT) k_rows_fwd(const R* __restrict__ in, c
   const cx<R>* src = reinterpret_cast<const cx<R>*>(in);
   for (int e = threadIdx.x; e < ROWS * n; e += FFT_NT) {
     const int r = e / n, m = e % n;
-    if (row0 + r < rows) cp_async_elem(buf + padded<PAD>(e), src + (size_t)(row0 + r) * n + m);
+    if (row0 + r < rows && (!PADIN || m < n / 2))
+      cp_async_elem(buf + padded<PAD>(e), src + (size_t)(row0 + r) * (PADIN ? n / 2 : n) + m);
     else buf[padded<PAD>(e)] = mk<R>(0, 0);
   }
   cp_async_wait_all();
@@ -186,6 +190,7 @@ __global__ void __launch_bounds__(FFT_NT) k_rows_fwd(const R* __restrict__ in, c
   for (int e = threadIdx.x; e < ROWS * n; e += FFT_NT) {
     const int r = e / n, k = e % n;
     if (row0 + r >= rows) continue;
+    const size_t orow = PADIN ? (size_t)((row0 + r) / (N / 2)) * N + (row0 + r) % (N / 2) : (size_t)(row0 + r);
     const cx<R> Zk = buf[padded<PAD>(r * n + k)];
     cx<R> P;
     if (k == 0) {
@@ -197,14 +202,16 @@ __global__ void __launch_bounds__(FFT_NT) k_rows_fwd(const R* __restrict__ in, c
       const cx<R> O = mk<R>((R)0.5 * D.y, (R)-0.5 * D.x);  // D / (2i)
       P = cadd<R>(E, cmul<R>(tw[k], O));
     }
-    out[(size_t)(row0 + r) * n + k] = P;
+    out[orow * n + k] = P;
   }
 }
 
 // ---------------------------------------------------------------------------
 // rows_inv: packed half spectrum rows -> real rows (times N).
 // ---------------------------------------------------------------------------
-template <class R, int N>
+// CROP: only rows 0..N/2-1 of each band (rows = (N/2) L; row r of band l read
+// from row l N + r) and only their first N/2 values, written with pitch N/2.
+template <class R, int N, bool CROP = false>
 __global__ void __launch_bounds__(FFT_NT) k_rows_inv(const cx<R>* __restrict__ in, R* __restrict__ out,
                                                      int rows, const cx<R>* __restrict__ tw) {
   constexpr int n = N / 2;
@@ -216,7 +223,8 @@ __global__ void __launch_bounds__(FFT_NT) k_rows_inv(const cx<R>* __restrict__ i
   const int row0 = blockIdx.x * ROWS;
   for (int e = threadIdx.x; e < ROWS * n; e += FFT_NT) {
     const int r = e / n, m = e % n;
-    if (row0 + r < rows) cp_async_elem(buf + padded<PAD>(e), in + (size_t)(row0 + r) * n + m);
+    const size_t irow = CROP ? (size_t)((row0 + r) / (N / 2)) * N + (row0 + r) % (N / 2) : (size_t)(row0 + r);
+    if (row0 + r < rows) cp_async_elem(buf + padded<PAD>(e), in + irow * n + m);
     else buf[padded<PAD>(e)] = mk<R>(0, 0);
   }
   cp_async_wait_all();
@@ -252,9 +260,9 @@ __global__ void __launch_bounds__(FFT_NT) k_rows_inv(const cx<R>* __restrict__ i
   cx<R>* dst = reinterpret_cast<cx<R>*>(out);
   for (int e = threadIdx.x; e < ROWS * n; e += FFT_NT) {
     const int r = e / n, m = e % n;
-    if (row0 + r >= rows) continue;
+    if (row0 + r >= rows || (CROP && m >= n / 2)) continue;
     const cx<R> y = buf[padded<PAD>(e)];
-    dst[(size_t)(row0 + r) * n + m] = mk<R>(y.x, -y.y);  // x[2m] = Re conj(y), x[2m+1] = Im conj(y)
+    dst[(size_t)(row0 + r) * (CROP ? n / 2 : n) + m] = mk<R>(y.x, -y.y);  // x[2m] = Re conj(y), x[2m+1] = Im conj(y)
   }
 }
 
@@ -295,7 +303,10 @@ struct ColFilter {
   }
 };
 
-template <class R, int N, int MODE>
+// PRUNE (MODE 3 / 5): the spatial rows N/2..N-1 of the input are zero (they
+// are not read) and only the output rows 0..N/2-1 are written (a zero-padded
+// image in, its [0, N/2) rows out).
+template <class R, int N, int MODE, bool PRUNE = false>
 __global__ void __launch_bounds__(COLS_NT, 2) k_cols(cx<R>* __restrict__ work, const cx<R>* __restrict__ tw,
                                                   cx<R>* __restrict__ out_main, cx<R>* __restrict__ out_nyq,
                                                   const cx<R>* __restrict__ cc, const cx<R>* __restrict__ cc_nyq,
@@ -314,7 +325,8 @@ __global__ void __launch_bounds__(COLS_NT, 2) k_cols(cx<R>* __restrict__ work, c
   cx<R>* base = work + (size_t)band * N * n + kx0;
   for (int e = threadIdx.x; e < EL; e += COLS_NT) {
     const int ky = e / SW, c = e % SW;
-    cp_async_elem(buf + e, base + (size_t)ky * n + c);
+    if (PRUNE && ky >= N / 2) buf[e] = mk<R>(0, 0);
+    else cp_async_elem(buf + e, base + (size_t)ky * n + c);
   }
   if (MODE != 0) {
     // L2 prefetch of the strip's filter constants (read after the forward
@@ -386,6 +398,7 @@ __global__ void __launch_bounds__(COLS_NT, 2) k_cols(cx<R>* __restrict__ work, c
     fft_all<R, N, 1, SW, COLS_NT, 1, SW, true, 1>(buf, tw);
     for (int e = threadIdx.x; e < EL; e += COLS_NT) {
       const int ky = e / SW, c = e % SW;
+      if (PRUNE && ky >= N / 2) continue;
       base[(size_t)ky * n + c] = cconj<R>(buf[e]);
     }
     if (MODE == 2) {
@@ -459,6 +472,38 @@ static cudaError_t cols_n(cx<R>* work, int L, const cx<R>* tw, int mode, cx<R>* 
   return cols_mode<R, N, 2>(work, L, tw, om, on, cc, ccn, gg, ggn, hh, hhn, yh, yhn, partials, s);
 }
 
+template <class R, int N, bool PADIN>
+static cudaError_t rows_fwd_v(const R* in, cx<R>* out, int rows, const cx<R>* tw, cudaStream_t s) {
+  constexpr int ROWS = RowCfg<R, N>::ROWS;
+  const size_t sm = sizeof(cx<R>) * RowCfg<R, N>::SLOTS;
+  cudaError_t e = cudaFuncSetAttribute(k_rows_fwd<R, N, PADIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_rows_fwd<R, N, PADIN><<<(rows + ROWS - 1) / ROWS, FFT_NT, sm, s>>>(in, out, rows, tw);
+  return cudaGetLastError();
+}
+template <class R, int N, bool CROP>
+static cudaError_t rows_inv_v(const cx<R>* in, R* out, int rows, const cx<R>* tw, cudaStream_t s) {
+  constexpr int ROWS = RowCfg<R, N>::ROWS;
+  const size_t sm = sizeof(cx<R>) * RowCfg<R, N>::SLOTS;
+  cudaError_t e = cudaFuncSetAttribute(k_rows_inv<R, N, CROP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_rows_inv<R, N, CROP><<<(rows + ROWS - 1) / ROWS, FFT_NT, sm, s>>>(in, out, rows, tw);
+  return cudaGetLastError();
+}
+template <class R, int N, int MODE>
+static cudaError_t cols_pruned_v(cx<R>* work, int L, const cx<R>* tw, const cx<R>* hh, const cx<R>* hhn,
+                                 cudaStream_t s) {
+  constexpr int SW = ColCfg<R, N>::SW;
+  const size_t sm = sizeof(cx<R>) * N * SW;
+  const int blocks = L * ((N / 2) / SW);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_cols<R, N, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_cols<R, N, MODE, true><<<blocks, COLS_NT, sm, s>>>(work, tw, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                       nullptr, hh, hhn, nullptr, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
 template <class R>
 int cols_blocks(int N, int L) {
   const int sw0 = (sizeof(R) == 4 ? 8192 : 4096) / N;
@@ -512,6 +557,49 @@ cudaError_t launch_constants(const cx<R>* hh, const cx<R>* hh_nyq, const cx<R>* 
       hh, yh, cc, gg, cm, (R)rho_bar, invN2);
   k_constants<R><<<(unsigned)((cn + 255) / 256), 256, 0, s>>>(hh_nyq, yh_nyq, cc_nyq, gg_nyq, cn, (R)rho_bar, invN2);
   return cudaGetLastError();
+}
+
+// The zero-padded 2-D convolution of an (M/2) x (M/2) image through M x M
+// transforms that skip what is known to be zero or not needed (FP32): rows of
+// the padded image in, the column pass on the first M/2 spatial rows, the
+// [0, M/2)^2 region out (see the PADIN, PRUNE and CROP variants above).
+#define MF_SWITCH_M(M, CALL)          \
+  switch (M) {                        \
+    case 32: return CALL(32);         \
+    case 64: return CALL(64);         \
+    case 128: return CALL(128);       \
+    case 256: return CALL(256);       \
+    case 512: return CALL(512);       \
+    case 1024: return CALL(1024);     \
+    case 2048: return CALL(2048);     \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t launch_rows_fwd_pad(const float* in, cx<float>* out, int M, int rows, const cx<float>* tw,
+                                cudaStream_t s) {
+#define CALL(MM) rows_fwd_v<float, MM, true>(in, out, rows, tw, s)
+  MF_SWITCH_M(M, CALL)
+#undef CALL
+}
+cudaError_t launch_rows_inv_crop(const cx<float>* in, float* out, int M, int rows, const cx<float>* tw,
+                                 cudaStream_t s) {
+#define CALL(MM) rows_inv_v<float, MM, true>(in, out, rows, tw, s)
+  MF_SWITCH_M(M, CALL)
+#undef CALL
+}
+cudaError_t launch_cols_pruned(cx<float>* work, int M, int L, const cx<float>* tw, int mode, const cx<float>* hh,
+                               const cx<float>* hh_nyq, cudaStream_t s) {
+  if (mode == 3) {
+#define CALL(MM) cols_pruned_v<float, MM, 3>(work, L, tw, hh, hh_nyq, s)
+    MF_SWITCH_M(M, CALL)
+#undef CALL
+  }
+  if (mode == 5) {
+#define CALL(MM) cols_pruned_v<float, MM, 5>(work, L, tw, hh, hh_nyq, s)
+    MF_SWITCH_M(M, CALL)
+#undef CALL
+  }
+  return cudaErrorInvalidValue;
 }
 
 #define INST(R)                                                                                          \

@@ -175,6 +175,16 @@ template <class R> cudaError_t launch_cols(cx<R>* work, int N, int L, const cx<R
 template <class R> int cols_blocks(int N, int L);
 // Row-wise inverse: packed half spectrum in -> real rows out (scaled by N).
 template <class R> cudaError_t launch_rows_inv(const cx<R>* in, R* out, int N, int rows, const cx<R>* tw, cudaStream_t s);
+// Zero-padded convolution at transform length M (FP32): rows of (M/2)-wide
+// images padded to M (rows = (M/2) L, output rows l M + r), the column pass
+// with transfer function hh (mode 3) or its conjugate (mode 5) on the first
+// M/2 spatial rows, and the inverse rows cropped to the [0, M/2)^2 region.
+cudaError_t launch_rows_fwd_pad(const float* in, cx<float>* out, int M, int rows, const cx<float>* tw,
+                                cudaStream_t s);
+cudaError_t launch_cols_pruned(cx<float>* work, int M, int L, const cx<float>* tw, int mode, const cx<float>* hh,
+                               const cx<float>* hh_nyq, cudaStream_t s);
+cudaError_t launch_rows_inv_crop(const cx<float>* in, float* out, int M, int rows, const cx<float>* tw,
+                                 cudaStream_t s);
 // g and c of the Fourier-diagonal solve.
 template <class R> cudaError_t launch_constants(const cx<R>* hh, const cx<R>* hh_nyq, const cx<R>* yh,
                                                 const cx<R>* yh_nyq, cx<R>* cc, cx<R>* cc_nyq, R* gg,
@@ -234,11 +244,11 @@ cudaError_t linear_fit(mf_plan* p, const float* y, double* partials, int* nblock
 
 // Visibility operator (vis.cu): plan-time Toeplitz kernels (into h2), the
 // per-call dirty image Re(Phi^H W y) (into cgv) and 1/2 sum w |y|^2, and the
-// data-fit partials from A X held in big (residual iterations).
+// data-fit partials from A X (residual iterations).
 size_t vis_spec_elems(int N);
 cudaError_t vis_setup(mf_plan* p, const int* counts);
 cudaError_t vis_dirty(mf_plan* p, const float* y, cudaStream_t s);
-cudaError_t vis_fit(mf_plan* p, double* partials, int* nblocks, cudaStream_t s);
+cudaError_t vis_fit(mf_plan* p, const float* ax, double* partials, int* nblocks, cudaStream_t s);
 
 // Dual residual of residual iterations (dual.cu): cubes of p->dual, the
 // snapshot taken before step I, and the reduction after the iteration.

@@ -24,6 +24,8 @@
 // sum_m w_m |c_m|, below FP32 rounding of the result.
 //
 // The data-fit term of the objective is 1/2 x^T (Q_l - rho I) x - x^T d + 1/2 sum_m w_m |y_m|^2.
+// The CG operator's 2N convolution skips the padding zeros and the discarded
+// outputs (cg.cu, conv2n).
 
 #include <cmath>
 #include <vector>
@@ -160,19 +162,18 @@ __global__ void k_vis_check(const float2* __restrict__ uv, const float* __restri
   }
 }
 
-// Data-fit partials 1/2 x.(A x) - x.d per band and chunk (A x in the [0,N)^2
-// region of big), plus 1/2 sum w |y|^2 in the first block.
-__global__ void __launch_bounds__(VNT) k_vis_fit(const float* __restrict__ X, const float* __restrict__ big,
+// Data-fit partials 1/2 x.(A x) - x.d per band and chunk (A x: ax, [L][N][N]),
+// plus 1/2 sum w |y|^2 in the first block.
+__global__ void __launch_bounds__(VNT) k_vis_fit(const float* __restrict__ X, const float* __restrict__ ax_cube,
                                                  const float* __restrict__ d, const double* __restrict__ c0, int N,
                                                  double* __restrict__ partials) {
-  const int band = blockIdx.y, M = 2 * N;
+  const int band = blockIdx.y;
   const size_t NN = (size_t)N * N;
   float s = 0.0f;
   for (size_t e = blockIdx.x * (size_t)VNT + threadIdx.x; e < NN; e += (size_t)gridDim.x * VNT) {
     const size_t i = (size_t)band * NN + e;
-    const int r = (int)(e / N), c = (int)(e % N);
     const float x = X[i];
-    const float ax = big[((size_t)band * M + r) * M + c];
+    const float ax = ax_cube[i];
     s = fmaf(x, fmaf(0.5f, ax, -d[i]), s);
   }
   float q[Q_COUNT];
@@ -372,10 +373,9 @@ cudaError_t vis_dirty(mf_plan* p, const float* y, cudaStream_t s) {
   return e;
 }
 
-cudaError_t vis_fit(mf_plan* p, double* partials, int* nblocks, cudaStream_t s) {
+cudaError_t vis_fit(mf_plan* p, const float* ax, double* partials, int* nblocks, cudaStream_t s) {
   const dim3 g(MF_CG_CHUNKS, p->L);
-  k_vis_fit<<<g, VNT, 0, s>>>((const float*)p->X, (const float*)p->big, (const float*)p->cgv, p->vis_c0, p->N,
-                              partials);
+  k_vis_fit<<<g, VNT, 0, s>>>((const float*)p->X, ax, (const float*)p->cgv, p->vis_c0, p->N, partials);
   *nblocks = MF_CG_CHUNKS * p->L;
   return cudaGetLastError();
 }
