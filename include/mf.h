@@ -146,6 +146,19 @@ mf_status mf_plan_create_linear(int N, int L, const float* psf_cube, mf_plan** o
  * point or weight out of range or not finite), MF_ERR_OOM, MF_ERR_CUDA. */
 mf_status mf_plan_create_vis(int N, int L, const int* n_vis, const float* uv, const float* weights,
                              mf_plan** out);
+
+/* Model visibilities of a plan from mf_plan_create_vis: vis_out = Phi_l x_l for
+ * every band (the operator of mf_plan_create_vis, Section 2's last paragraph),
+ * by a type-2 non-uniform FFT with the same gridding kernel: x divided by the
+ * kernel's transform on the 2x oversampled grid, the grid's FFT, interpolation
+ * at each uv point (about 1e-7 of sum |x| from the exact sum).
+ *   x       : device float [L][N][N], or NULL for the plan's X
+ *   vis_out : device float [sum n_vis][2] (re, im), the plan's visibility order
+ *   stream  : cudaStream_t; the call first waits for the plan's last stream
+ *             (it uses the plan's work arrays) and becomes the plan's stream
+ * Asynchronous.  Errors: MF_ERR_INVALID (not a visibility plan, NULL vis_out),
+ * the plan's latched status, MF_ERR_CUDA. */
+mf_status mf_vis_predict(mf_plan* p, const float* x, float* vis_out, void* stream);
 /* Frees everything the plan owns; NULL is a no-op.  Synchronises the device. */
 void mf_plan_destroy(mf_plan* p);
 size_t mf_plan_device_bytes(const mf_plan* p);

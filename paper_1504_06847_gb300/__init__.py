@@ -26,7 +26,7 @@ EXPORTS = ["mf_params_default", "mf_plan_create", "mf_plan_create_f64", "mf_plan
            "mf_wavelet_filter", "mf_status_string", "mf_plan_set_timing", "mf_plan_get_timing",
            "mf_kernel_name", "mf_xstep_noalloc", "mf_plan_set_option", "mf_batch_iterate",
            "mf_admm_backward", "mf_plan_clear_status", "mf_spectral_index", "mf_plan_create_linear",
-           "mf_spectral_basis", "mf_plan_create_vis"]
+           "mf_spectral_basis", "mf_plan_create_vis", "mf_vis_predict"]
 MF_OPT_WAV_TILE, MF_OPT_TEST_TC_STALL = 0, 1
 
 KERNELS = ["rows_fwd", "cols_solve", "rows_inv", "spectral", "wav_ll", "wav_level1", "wav_levelj", "setup",
@@ -79,6 +79,8 @@ def lib():
         L.mf_plan_create_vis.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp, vp,
                                          ctypes.POINTER(vp)]
         L.mf_plan_create_vis.restype = ctypes.c_int
+        L.mf_vis_predict.argtypes = [vp, vp, vp, vp]
+        L.mf_vis_predict.restype = ctypes.c_int
         L.mf_plan_destroy.argtypes = [vp]
         L.mf_plan_destroy.restype = None
         L.mf_plan_device_bytes.argtypes = [vp]
@@ -276,6 +278,25 @@ class Plan:
                                         ctypes.byref(h)), "mf_plan_create_vis")
         self._h = h
         return self
+
+    def predict(self, x=None):
+        """Model visibilities Phi x of a visibility plan (see mf_vis_predict): x a
+        float32 CUDA tensor [L, N, N] or None for the plan's X; returns complex64
+        [sum M_l] in the plan's visibility order."""
+        import torch
+
+        if self.n_vis is None:
+            raise ValueError("predict needs a plan from Plan.from_visibilities")
+        if x is not None:
+            if x.dtype != torch.float32 or not x.is_cuda or tuple(x.shape) != (self.L, self.N, self.N):
+                raise ValueError("x must be a float32 CUDA tensor [L, N, N]")
+            x = x.contiguous()
+        out = torch.empty((self.n_vis, 2), dtype=torch.float32, device=self.device)
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        _check(lib().mf_vis_predict(self._h, ctypes.c_void_p(x.data_ptr()) if x is not None else None,
+                                    ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s)), "mf_vis_predict")
+        self._x_keepalive = x
+        return torch.view_as_complex(out)
 
     def __init__(self, psf, linear: bool = False):
         import torch

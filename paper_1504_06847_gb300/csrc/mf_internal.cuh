@@ -249,6 +249,7 @@ size_t vis_spec_elems(int N);
 cudaError_t vis_setup(mf_plan* p, const int* counts);
 cudaError_t vis_dirty(mf_plan* p, const float* y, cudaStream_t s);
 cudaError_t vis_fit(mf_plan* p, const float* ax, double* partials, int* nblocks, cudaStream_t s);
+cudaError_t vis_predict(mf_plan* p, const float* x, float* out, cudaStream_t s);
 
 // Dual residual of residual iterations (dual.cu): cubes of p->dual, the
 // snapshot taken before step I, and the reduction after the iteration.

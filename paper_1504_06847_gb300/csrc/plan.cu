@@ -867,6 +867,26 @@ mf_status mf_plan_create_vis(int N, int L, const int* n_vis, const float* uv, co
   return MF_OK;
 }
 
+mf_status mf_vis_predict(mf_plan* p, const float* x, float* vis_out, void* stream) {
+  if (!p || !p->vis || !vis_out) return MF_ERR_INVALID;
+  if (p->status != MF_OK) return p->status;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the call shares the plan's work arrays: it runs after the plan's last work
+  if (s != p->stream && cudaStreamSynchronize(p->stream) != cudaSuccess) {
+    cudaGetLastError();
+    p->status = MF_ERR_CUDA;
+    return p->status;
+  }
+  p->stream = s;
+  if (p->vis_off.back() == 0) return MF_OK;
+  if (vis_predict(p, x ? x : (const float*)p->X, vis_out, s) != cudaSuccess) {
+    cudaGetLastError();
+    p->status = MF_ERR_CUDA;
+    return p->status;
+  }
+  return MF_OK;
+}
+
 void mf_plan_destroy(mf_plan* p) {
   if (!p) return;
   cudaDeviceSynchronize();

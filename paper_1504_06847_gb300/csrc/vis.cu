@@ -13,6 +13,10 @@
 // kernel embedded at offsets d mod 2N, p at [0,N)^2, the output cropped to
 // [0,N)^2): one 2N FFT round trip per CG iteration, no gridding in the loop.
 //
+// The forward operator itself (model visibilities, mf_vis_predict) is the
+// type-2 transform with the same kernel: the image divided by the kernel's
+// transform on the oversampled grid, its FFT, and interpolation at each point.
+//
 // k (once per plan) and the dirty image d = Re(Phi^H W y) (once per call) are
 // type-1 non-uniform FFTs, computed by gridding with the "exponential of
 // semicircle" kernel phi(z) = exp(beta (sqrt(1 - z^2) - 1)) (Barnett, Magland
@@ -130,6 +134,56 @@ __global__ void __launch_bounds__(VNT) k_vis_dirty_gather(const C* __restrict__ 
   const float2 fr = spec_at(main, nyq, G, ky, kx);
   const float2 fi = spec_at(main + (size_t)G * h, nyq + G, G, ky, kx);
   out[t] = (fr.x + fi.y) / (phihat[r] * phihat[c]);
+}
+
+// Forward operator (type-2 non-uniform FFT, the same kernel): the image's
+// modes k = (r - N/2, c - N/2), divided by phi^(k_y) phi^(k_x), at k mod G of a
+// real G x G grid (G = 2N), zero elsewhere; one thread per grid cell.
+__global__ void __launch_bounds__(VNT) k_vis_modes(const float* __restrict__ x, const float* __restrict__ phihat,
+                                                   int N, float* __restrict__ grid) {
+  const int G = 2 * N;
+  const long t = blockIdx.x * (long)VNT + threadIdx.x;
+  if (t >= (long)G * G) return;
+  const int gy = (int)(t / G), gx = (int)(t % G);
+  // grid index -> mode -> image index (rows and columns N/2 .. G - N/2 - 1 are empty)
+  const int r = gy < N / 2 ? gy + N / 2 : gy - G + N / 2;
+  const int c = gx < N / 2 ? gx + N / 2 : gx - G + N / 2;
+  float v = 0.0f;
+  if (r >= 0 && r < N && c >= 0 && c < N) v = x[(size_t)r * N + c] / (phihat[r] * phihat[c]);
+  grid[t] = v;
+}
+
+// (Phi x)_m = sum over the VW x VW cells j nearest g = 2 (u_m, v_m) of
+// phi(2 (j_y - g_y) / VW) phi(2 (j_x - g_x) / VW) F(j), F the forward DFT of the
+// mode grid (sum_k grid_k e^{-2 pi i k.j / G}); one thread per visibility.
+__global__ void __launch_bounds__(VNT) k_vis_interp(const float2* __restrict__ uv, const C* __restrict__ main,
+                                                    const C* __restrict__ nyq, int count, int G, float scale,
+                                                    float2* __restrict__ out) {
+  const int m = blockIdx.x * VNT + threadIdx.x;
+  if (m >= count) return;
+  const float2 q = uv[m];
+  const float gx = q.x * scale, gy = q.y * scale;
+  const float jx0 = ceilf(gx - 0.5f * VW), jy0 = ceilf(gy - 0.5f * VW);
+  float px[VW];
+#pragma unroll
+  for (int c = 0; c < VW; c++) px[c] = es_kernel((jx0 + (float)c - gx) * (2.0f / VW));
+  float sr = 0.0f, si = 0.0f;
+  for (int a = 0; a < VW; a++) {
+    const float jy = jy0 + (float)a;
+    const float py = es_kernel((jy - gy) * (2.0f / VW));
+    const int iy = (((int)jy % G) + G) % G;
+    float rr = 0.0f, ri = 0.0f;
+#pragma unroll
+    for (int c = 0; c < VW; c++) {
+      const int ix = (((int)(jx0 + (float)c) % G) + G) % G;
+      const float2 f = spec_at(main, nyq, G, iy, ix);
+      rr = fmaf(px[c], f.x, rr);
+      ri = fmaf(px[c], f.y, ri);
+    }
+    sr = fmaf(py, rr, sr);
+    si = fmaf(py, ri, si);
+  }
+  out[m] = make_float2(sr, si);
 }
 
 // 1/2 sum_m w_m |y_m|^2 in FP64, one block, fixed order
@@ -367,6 +421,31 @@ cudaError_t vis_dirty(mf_plan* p, const float* y, cudaStream_t s) {
     if (!e) {
       k_vis_dirty_gather<<<blocks_for((long)N * N), VNT, 0, s>>>(spec, spec_nyq, (const float*)p->vis_phihat, N,
                                                                   (float*)p->cgv + (size_t)l * N * N);
+      e = cudaGetLastError();
+    }
+  }
+  return e;
+}
+
+// out = Phi x for every band (x: [L][N][N]; out: the plan's visibility order),
+// band by band through big (the mode grid), work2 (row transforms) and vis_spec.
+cudaError_t vis_predict(mf_plan* p, const float* x, float* out, cudaStream_t s) {
+  const int N = p->N, L = p->L, G = 2 * N;
+  float* grid = (float*)p->big;
+  C* work = (C*)p->work2;
+  C* spec = (C*)p->vis_spec;
+  C* spec_nyq = (C*)p->vis_nyq;
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < L && !e; l++) {
+    const int cnt = p->vis_off[l + 1] - p->vis_off[l];
+    if (cnt == 0) continue;
+    k_vis_modes<<<blocks_for((long)G * G), VNT, 0, s>>>(x + (size_t)l * N * N, (const float*)p->vis_phihat, N,
+                                                          grid);
+    e = cudaGetLastError();
+    if (!e) e = grid_fft(grid, G, 1, work, spec, spec_nyq, (const C*)p->vis_twM, s);
+    if (!e) {
+      k_vis_interp<<<blocks_for(cnt), VNT, 0, s>>>((const float2*)p->vis_uv + p->vis_off[l], spec, spec_nyq, cnt,
+                                                    G, 2.0f, (float2*)out + p->vis_off[l]);
       e = cudaGetLastError();
     }
   }

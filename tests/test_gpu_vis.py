@@ -22,6 +22,8 @@ objective + 1/2 sum w |y|^2.  Inputs are rounded to FP32 before both sides see
 them.
 """
 
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -189,3 +191,45 @@ def test_all_visibilities_at_the_origin():
     assert max(errs.values()) < 1e-5, errs
     for l in range(3):  # the dirty image of band l is the constant Re(sum_m w_m y_m)
         assert np.ptp(d[l]) <= 1e-5 * np.abs(d[l]).max()
+
+
+@pytest.mark.parametrize("N,L,ants", [(64, 3, 24), (512, 2, 20)])
+def test_predict_matches_the_oracle_operator(N, L, ants):
+    # mf_vis_predict (type-2 non-uniform FFT, about 1e-7 of sum |x|) against the exact sum
+    c = synth.make_visibilities(N, L, n_sources=4, n_antennas=ants, seed=99 + N, random_weights=True)
+    pb = _problem(N, c, 1)
+    x = np.random.default_rng(N).uniform(0.0, 1.0, size=(L, N, N)).astype(np.float32)
+    ref = pb.apply_H(x.astype(np.float64))
+    plan = _plan(N, c)
+    got = plan.predict(torch.tensor(x, device="cuda")).cpu().numpy().astype(np.complex128)
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    _gpu.log_errors({"predict": float(err)})
+    assert err < 1e-5, err
+
+
+def test_predicted_residual_gives_the_data_fit():
+    # 1/2 sum w |y - Phi X|^2 from the model visibilities of the plan's X equals the
+    # oracle's data-fit term for its X (X agrees to ~1e-6; the fit is a difference
+    # ten times smaller than y at 20 dB, hence the 1e-4 bound)
+    c = synth.make_visibilities(64, 3, n_sources=4, n_antennas=24, seed=100, random_weights=True)
+    pb = _problem(64, c, 6)
+    st, _ = pb.run(4)
+    plan = _plan(64, c)
+    plan.iterate(_y(c), 4, cg_iters=6, **PRM)
+    vis, w = _f32(c)
+    y = np.concatenate(vis)
+    wc = np.concatenate(w)
+    model = plan.predict().cpu().numpy().astype(np.complex128)
+    fit_gpu = 0.5 * np.sum(wc * np.abs(y - model) ** 2)
+    fit_ref = 0.5 * np.sum(wc * np.abs(y - pb.apply_H(st["X"])) ** 2)
+    _gpu.log_errors({"fit": float(abs(fit_gpu - fit_ref) / fit_ref)})
+    assert abs(fit_gpu - fit_ref) < 1e-4 * fit_ref, (fit_gpu, fit_ref)
+
+
+def test_predict_rejects_other_plans():
+    c = synth.make_cube(32, 4, n_sources=2, n_antennas=16, seed=3)
+    plan = mf.Plan(torch.tensor(c.psf, dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError):
+        plan.predict()
+    out = torch.empty(8, device="cuda")
+    assert mf.lib().mf_vis_predict(plan._h, None, ctypes.c_void_p(out.data_ptr()), None) == mf.MF_ERR_INVALID
