@@ -258,7 +258,8 @@ const char* mf_kernel_name(int kernel);
 
 /* Options of a plan (each call synchronises the plan's last stream).
  *   MF_OPT_WAV_TILE: output tile edge of the fused wavelet level kernels,
- *                    64 (default) or 32; levels smaller than the tile use
+ *                    64 (default of FP32 plans) or 32 (default of FP64 plans,
+ *                    whose 64-wide kernels spill registers); levels smaller than the tile use
  *                    the largest tile that fits.  Launch shape only: every
  *                    value computes the same arithmetic per element in the
  *                    same order, so results are bitwise identical.
