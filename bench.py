@@ -384,8 +384,8 @@ def measure_forms(stream, xstep_ms=None):
 # convolution: two convolutions per operator application; visibilities: one.
 CG_BYTES = {"linear": 2 * 56 + 48, "vis": 56 + 48}
 # the spectral step with the Chebyshev basis added: X in; Gamma_P, S, Gamma_V,
-# Gamma_V2, Gamma_S in and out; b out
-SPECTRAL_B2_BYTES = 4 + 5 * 8 + 4
+# Gamma_V2, Gamma_S and S in the Chebyshev basis in and out; b out
+SPECTRAL_B2_BYTES = 4 + 6 * 8 + 4
 
 
 def measure_widened_rows(stream, plan, y, peak):

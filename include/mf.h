@@ -224,7 +224,11 @@ mf_status mf_plan_get_array(mf_plan* p, int which, void* dst, size_t* count);
 mf_status mf_plan_set_array(mf_plan* p, int which, const void* src, size_t count);
 
 /* Whole ADMM state (every array above, Gamma_V2 included) as one opaque device buffer for
- * checkpoint and warm restart.  With buf == NULL *bytes receives the size. */
+ * checkpoint and warm restart.  With buf == NULL *bytes receives the size.  The
+ * buffer does not record the dictionaries it was made with: after
+ * mf_plan_set_state (into the same plan or a new one of the same N, L and type)
+ * the next warm start continues with the wavelet and spectral dictionaries the
+ * caller passes, which must be those the state was made with. */
 mf_status mf_plan_get_state(mf_plan* p, void* buf, size_t* bytes);
 mf_status mf_plan_set_state(mf_plan* p, const void* buf, size_t bytes);
 

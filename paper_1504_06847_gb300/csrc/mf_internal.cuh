@@ -81,6 +81,8 @@ struct mf_plan {
   void* Sd;          // S W_nu
   void* GV;          // Gamma_V (DCT basis of the spectral dictionary)
   void* GV2;         // Gamma_V of the Chebyshev basis (spectral_mask bit 1)
+  void* S2;          // M S^: S in the Chebyshev basis (plans that used it; derived state)
+  int s2_valid;       // S2 equals M S^ (cleared when the state is set from outside)
   void* Mb2;         // L x L change of basis DCT domain -> Chebyshev basis (C2 C^T)
   int spectral_mask; // spectral dictionary of the current call
   void* GSd;         // Gamma_S W_nu
@@ -196,9 +198,12 @@ template <class R> cudaError_t launch_spectral(const R* X, R* GP, R* Sd, R* GV, 
                                                double* partials, int resid, cudaStream_t s);
 template <class R> int spectral_blocks(int N, int L);
 // The spectral step with the Chebyshev basis in the dictionary (DCT too when dct_on), L <= 64.
-template <class R> cudaError_t launch_spectral_b2(const R* X, R* GP, R* Sd, R* GV, R* GV2, R* GSd, R* b,
+template <class R> cudaError_t launch_spectral_b2(const R* X, R* GP, R* Sd, R* GV, R* GV2, R* GSd, R* S2, R* b,
                                                   const R* dctC, const R* Mb, int dct_on, int N, int L,
                                                   IterScalars<R> sc, double* partials, int resid, cudaStream_t s);
+// S2 = M S^ (S in the second spectral basis) from the DCT-domain S, after the
+// state was set from outside.
+template <class R> cudaError_t launch_s2_from_sd(const R* Mb, const R* Sd, R* S2, int N, int L, cudaStream_t s);
 
 // Wavelet analysis of the low-low band: LL_j (M/2 x M/2) from the M x M input.
 template <class R> cudaError_t launch_wav_ll(const R* in, size_t in_band_stride, size_t in_basis_stride,

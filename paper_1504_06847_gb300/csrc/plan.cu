@@ -96,7 +96,7 @@ void free_plan_memory(mf_plan* p) {
                   p->hhat_nyq,
                   p->yhat, p->yhat_nyq, p->cc, p->cc_nyq, p->gg, p->gg_nyq, p->tw, p->dctC, p->scratch,
                   p->partials, p->sums, p->wset, p->dct_tc, p->err, p->bwd_buf, p->dual, p->h2, p->h2_nyq,
-                  p->tw2, p->work2, p->big, p->cgv, p->cgs, p->cgpart, p->vis_uv, p->vis_w, p->vis_c0,
+                  p->tw2, p->work2, p->big, p->cgv, p->cgs, p->cgpart, p->vis_uv, p->vis_w, p->vis_c0, p->S2,
                   p->vis_phihat, p->vis_twM, p->vis_spec, p->vis_nyq};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -310,7 +310,8 @@ WavSet<R> make_wavset(unsigned mask, int* n_s) {
 template <class R>
 cudaError_t spectral_step(mf_plan* p, const IterScalars<R>& sc, int resid, int precision, cudaStream_t s) {
   if (p->spectral_mask & 2)
-    return launch_spectral_b2<R>((const R*)p->X, (R*)p->GP, (R*)p->Sd, (R*)p->GV, (R*)p->GV2, (R*)p->GSd, (R*)p->b,
+    return launch_spectral_b2<R>((const R*)p->X, (R*)p->GP, (R*)p->Sd, (R*)p->GV, (R*)p->GV2, (R*)p->GSd, (R*)p->S2,
+                                 (R*)p->b,
                                  (const R*)p->dctC, (const R*)p->Mb2, p->spectral_mask & 1, p->N, p->L, sc,
                                  p->partials, resid, s);
   return launch_spectral<R>((const R*)p->X, (R*)p->GP, (R*)p->Sd, (R*)p->GV, (R*)p->GSd, (R*)p->b,
@@ -321,7 +322,8 @@ cudaError_t spectral_step<float>(mf_plan* p, const IterScalars<float>& sc, int r
                                  cudaStream_t s) {
   if (p->spectral_mask & 2)
     return launch_spectral_b2<float>((const float*)p->X, (float*)p->GP, (float*)p->Sd, (float*)p->GV,
-                                     (float*)p->GV2, (float*)p->GSd, (float*)p->b, (const float*)p->dctC,
+                                     (float*)p->GV2, (float*)p->GSd, (float*)p->S2, (float*)p->b,
+                                     (const float*)p->dctC,
                                      (const float*)p->Mb2, p->spectral_mask & 1, p->N, p->L, sc, p->partials, resid,
                                      s);
   if (precision == MF_FP32_DCT_SPLITBF16)
@@ -483,11 +485,24 @@ mf_status prepare(mf_plan* p, const R* y, const mf_params* prm, int n_iter, cuda
   sc.inv_rho_V = (R)(1.0 / prm->rho_V);
   const int m_nu = (prm->spectral_mask & 1) + ((prm->spectral_mask >> 1) & 1);  // bases of W_nu
   sc.inv_VS = (R)(1.0 / (m_nu * prm->rho_V + prm->rho_S));  // step V: m_nu rho_V + rho_S
-  if (prm->warm_start && p->nd_state != ws.nd && p->iters_done > 0)
+  if (prm->warm_start && p->nd_state >= 0 && p->nd_state != ws.nd && p->iters_done > 0)
     return MF_ERR_INVALID;  // the stored Gamma_T belongs to another dictionary
-  if (prm->warm_start && p->iters_done > 0 && p->spectral_mask != (int)prm->spectral_mask)
+  if (prm->warm_start && p->iters_done > 0 && p->spectral_mask != 0 && p->spectral_mask != (int)prm->spectral_mask)
     return MF_ERR_INVALID;  // the stored Gamma_V belongs to another spectral dictionary
   p->spectral_mask = (int)prm->spectral_mask;
+  if (!(prm->spectral_mask & 2)) {
+    p->s2_valid = 0;  // S2 is kept only while the Chebyshev basis is iterated
+  } else if (!p->S2) {
+    // S in the Chebyshev basis, kept by the plan from its first use on
+    const size_t bytes = p->cube * sizeof(R);
+    if (cudaMalloc(&p->S2, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p->S2 = nullptr;
+      return MF_ERR_OOM;
+    }
+    p->total_bytes += bytes;
+    p->s2_valid = 0;
+  }
   if (prm->resid_every > 0 && !p->dual) {
     // snapshots and work cubes of the dual residual, kept by the plan from now on
     const size_t bytes = dual_cubes() * p->cube * sizeof(R);
@@ -525,8 +540,16 @@ mf_status prepare(mf_plan* p, const R* y, const mf_params* prm, int n_iter, cuda
       for (void* q : z)
         if (!e) e = cudaMemsetAsync(q, 0, cb, s);
       if (!e) e = cudaMemsetAsync(p->GT[p->gt_cur], 0, cb * MF_MAX_BASES, s);
+      if (!e && (prm->spectral_mask & 2)) {
+        e = cudaMemsetAsync(p->S2, 0, cb, s);  // M S^ of the zero state
+        p->s2_valid = 1;
+      }
       p->iters_done = 0;
       p->report.resid_iter = -1;
+    }
+    if (!e && (prm->spectral_mask & 2) && !p->s2_valid) {
+      e = launch_s2_from_sd<R>((const R*)p->Mb2, (const R*)p->Sd, (R*)p->S2, N, L, s);
+      p->s2_valid = 1;
     }
   }
   if (e) {
@@ -939,6 +962,7 @@ mf_status mf_plan_set_array(mf_plan* p, int which, const void* src, size_t count
   if (!dst || count > n || (which != MF_ARR_GAMMA_T && count != n)) return MF_ERR_INVALID;
   if (cudaStreamSynchronize(p->stream) != cudaSuccess) return MF_ERR_CUDA;
   if (!copy_d2d(p, dst, src, count * p->esz)) return MF_ERR_CUDA;
+  if (which == MF_ARR_S_DCT) p->s2_valid = 0;
   if (which == MF_ARR_GAMMA_T) p->nd_state = (int)(count / p->cube);
   return MF_OK;
 }
@@ -976,6 +1000,11 @@ mf_status mf_plan_set_state(mf_plan* p, const void* buf, size_t bytes) {
   }
   if (!copy_d2d(p, p->GT[p->gt_cur], s, cb * MF_MAX_BASES)) return MF_ERR_CUDA;
   if (p->iters_done == 0) p->iters_done = 1;
+  p->s2_valid = 0;
+  // the dictionaries the state was made with are not recorded in it: the next
+  // warm start takes the caller's (the checks against the plan's last call are off)
+  p->nd_state = -1;
+  p->spectral_mask = 0;
   return MF_OK;
 }
 

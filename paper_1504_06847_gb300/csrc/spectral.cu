@@ -211,14 +211,16 @@ __global__ void __launch_bounds__(SP_NT) k_spectral(const R* __restrict__ X, R* 
 //   S^+ = ((Gamma_V + rho_V V) + M^T (Gamma_V2 + rho_V V2) - Gamma_S^ + rho_S X^)
 //         / (m_nu rho_V + rho_S)                                     (V)
 //   Gamma_V2 += rho_V (V2 - M S^+)                                   (VI, new S)
-// and the DCT terms as in k_spectral when DCT_ON.  Three more L x L products
-// per pixel spectrum (M S^, M^T Q2, M S^+), each staged through the shared tile.
+// and the DCT terms as in k_spectral when DCT_ON.  The plan keeps S2 = M S^ (S
+// in the second basis) beside S^: the old one is read for step IV, the new one
+// (computed for step VI anyway) written, so two L x L products per pixel
+// spectrum are added (M^T Q2, M S^+), each staged through the shared tile.
 template <class R, int LP, int RESID, bool DCT_ON>
 __global__ void __launch_bounds__(SP_NT) k_spectral_b2(const R* __restrict__ X, R* __restrict__ GP, R* __restrict__ Sd,
                                                         R* __restrict__ GV, R* __restrict__ GV2, R* __restrict__ GSd,
-                                                        R* __restrict__ b, const R* __restrict__ dctC,
-                                                        const R* __restrict__ Mb, int NN, int L, IterScalars<R> sc,
-                                                        double* __restrict__ partials) {
+                                                        R* __restrict__ S2, R* __restrict__ b,
+                                                        const R* __restrict__ dctC, const R* __restrict__ Mb, int NN,
+                                                        int L, IterScalars<R> sc, double* __restrict__ partials) {
   constexpr int PT = 4096 / LP;
   constexpr int TP = PT / 4;
   static_assert((LP / 4) * TP == SP_NT, "tile");
@@ -250,10 +252,10 @@ __global__ void __launch_bounds__(SP_NT) k_spectral_b2(const R* __restrict__ X, 
   };
   {
     // L2 prefetch of the tile's rows of the state arrays read after the first
-    // products (S, Gamma_V2, Gamma_V, Gamma_S, Gamma_P): one per 128-byte line
+    // product (S2, Gamma_V2, S, Gamma_S, Gamma_P, Gamma_V): one per 128-byte line
     constexpr int LINES = (PT * (int)sizeof(R) + 127) / 128;
-    const R* arr[5] = {Sd, GV2, GSd, GP, DCT_ON ? GV : Sd};
-    for (int e = tid; e < (DCT_ON ? 5 : 4) * L * LINES; e += SP_NT) {
+    const R* arr[6] = {S2, GV2, Sd, GSd, GP, DCT_ON ? GV : Sd};
+    for (int e = tid; e < (DCT_ON ? 6 : 5) * L * LINES; e += SP_NT) {
       const int a = e / (L * LINES), r = e % (L * LINES);
       const int l = r / LINES, ln = r % LINES;
       asm volatile("prefetch.global.L2 [%0];" ::"l"(arr[a] + (size_t)l * NN + p0 + ln * (128 / (int)sizeof(R))));
@@ -304,19 +306,19 @@ __global__ void __launch_bounds__(SP_NT) k_spectral_b2(const R* __restrict__ X, 
       for (int c = 0; c < 4; c++)
         if (kb + a < L && pix_ok) r_l1 += fabs(mx[a][c]) + (DCT_ON ? fabs(xh[a][c]) : (R)0);
   }
-  // basis-2 coefficients of the old S
-  __syncthreads();
-  load_tile(Sd);
-  __syncthreads();
+  // basis-2 coefficients of the old S (kept by the plan)
   R v2[4][4], g2[4][4], q2[4][4];
   {
     R w2[4][4];
-    product(MT, w2, kb, pb);
 #pragma unroll
     for (int a = 0; a < 4; a++) {
       const int k = kb + a;
-      if (k < L && pix_ok) V4<R>::ld(GV2 + (size_t)k * NN + p0 + pb, g2[a]);
-      else for (int c = 0; c < 4; c++) g2[a][c] = 0;
+      if (k < L && pix_ok) {
+        V4<R>::ld(GV2 + (size_t)k * NN + p0 + pb, g2[a]);
+        V4<R>::ld(S2 + (size_t)k * NN + p0 + pb, w2[a]);
+      } else {
+        for (int c = 0; c < 4; c++) g2[a][c] = w2[a][c] = 0;
+      }
 #pragma unroll
       for (int c = 0; c < 4; c++) {
         v2[a][c] = soft_thr<R>(w2[a][c] - g2[a][c] * sc.inv_rho_V, sc.tau_V);
@@ -387,6 +389,7 @@ __global__ void __launch_bounds__(SP_NT) k_spectral_b2(const R* __restrict__ X, 
       const int k = kb + a;
       if (k < L && pix_ok) {
         R gn[4];
+        V4<R>::st(S2 + (size_t)k * NN + p0 + pb, m2[a]);  // S2 of the new S
 #pragma unroll
         for (int c = 0; c < 4; c++) {
           gn[c] = g2[a][c] + sc.rho_V * (v2[a][c] - m2[a][c]);
@@ -449,8 +452,9 @@ __global__ void __launch_bounds__(SP_NT) k_spectral_b2(const R* __restrict__ X, 
 }
 
 template <class R, int LP, bool DCT_ON>
-static cudaError_t spectral_b2_lp(const R* X, R* GP, R* Sd, R* GV, R* GV2, R* GSd, R* b, const R* dctC, const R* Mb,
-                                  int N, int L, IterScalars<R> sc, double* partials, int resid, cudaStream_t s) {
+static cudaError_t spectral_b2_lp(const R* X, R* GP, R* Sd, R* GV, R* GV2, R* GSd, R* S2, R* b, const R* dctC,
+                                  const R* Mb, int N, int L, IterScalars<R> sc, double* partials, int resid,
+                                  cudaStream_t s) {
   constexpr int PT = 4096 / LP;
   const int NN = N * N;
   const int blocks = (NN + PT - 1) / PT;
@@ -459,19 +463,19 @@ static cudaError_t spectral_b2_lp(const R* X, R* GP, R* Sd, R* GV, R* GV2, R* GS
   if (resid) {
     e = cudaFuncSetAttribute(k_spectral_b2<R, LP, 1, DCT_ON>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_spectral_b2<R, LP, 1, DCT_ON><<<blocks, SP_NT, sm, s>>>(X, GP, Sd, GV, GV2, GSd, b, dctC, Mb, NN, L, sc,
+    k_spectral_b2<R, LP, 1, DCT_ON><<<blocks, SP_NT, sm, s>>>(X, GP, Sd, GV, GV2, GSd, S2, b, dctC, Mb, NN, L, sc,
                                                                partials);
   } else {
     e = cudaFuncSetAttribute(k_spectral_b2<R, LP, 0, DCT_ON>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_spectral_b2<R, LP, 0, DCT_ON><<<blocks, SP_NT, sm, s>>>(X, GP, Sd, GV, GV2, GSd, b, dctC, Mb, NN, L, sc,
+    k_spectral_b2<R, LP, 0, DCT_ON><<<blocks, SP_NT, sm, s>>>(X, GP, Sd, GV, GV2, GSd, S2, b, dctC, Mb, NN, L, sc,
                                                                partials);
   }
   return cudaGetLastError();
 }
 
 template <class R, bool DCT_ON>
-static cudaError_t spectral_b2_dispatch(const R* X, R* GP, R* Sd, R* GV, R* GV2, R* GSd, R* b, const R* dctC,
+static cudaError_t spectral_b2_dispatch(const R* X, R* GP, R* Sd, R* GV, R* GV2, R* GSd, R* S2, R* b, const R* dctC,
                                         const R* Mb, int N, int L, IterScalars<R> sc, double* partials, int resid,
                                         cudaStream_t s);
 
@@ -730,29 +734,54 @@ template int spectral_blocks<float>(int, int);
 template int spectral_blocks<double>(int, int);
 
 template <class R, bool DCT_ON>
-static cudaError_t spectral_b2_dispatch(const R* X, R* GP, R* Sd, R* GV, R* GV2, R* GSd, R* b, const R* dctC,
+static cudaError_t spectral_b2_dispatch(const R* X, R* GP, R* Sd, R* GV, R* GV2, R* GSd, R* S2, R* b, const R* dctC,
                                         const R* Mb, int N, int L, IterScalars<R> sc, double* partials, int resid,
                                         cudaStream_t s) {
   switch (padded_L(L)) {
-    case 8: return spectral_b2_lp<R, 8, DCT_ON>(X, GP, Sd, GV, GV2, GSd, b, dctC, Mb, N, L, sc, partials, resid, s);
-    case 16: return spectral_b2_lp<R, 16, DCT_ON>(X, GP, Sd, GV, GV2, GSd, b, dctC, Mb, N, L, sc, partials, resid, s);
-    case 32: return spectral_b2_lp<R, 32, DCT_ON>(X, GP, Sd, GV, GV2, GSd, b, dctC, Mb, N, L, sc, partials, resid, s);
-    case 64: return spectral_b2_lp<R, 64, DCT_ON>(X, GP, Sd, GV, GV2, GSd, b, dctC, Mb, N, L, sc, partials, resid, s);
+    case 8: return spectral_b2_lp<R, 8, DCT_ON>(X, GP, Sd, GV, GV2, GSd, S2, b, dctC, Mb, N, L, sc, partials, resid, s);
+    case 16: return spectral_b2_lp<R, 16, DCT_ON>(X, GP, Sd, GV, GV2, GSd, S2, b, dctC, Mb, N, L, sc, partials, resid, s);
+    case 32: return spectral_b2_lp<R, 32, DCT_ON>(X, GP, Sd, GV, GV2, GSd, S2, b, dctC, Mb, N, L, sc, partials, resid, s);
+    case 64: return spectral_b2_lp<R, 64, DCT_ON>(X, GP, Sd, GV, GV2, GSd, S2, b, dctC, Mb, N, L, sc, partials, resid, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
+// S2[k][p] = sum_l M[k][l] S^[l][p]: one thread per (band k, pixel p), pixels
+// fastest (coalesced); used only when the state was set from outside.
 template <class R>
-cudaError_t launch_spectral_b2(const R* X, R* GP, R* Sd, R* GV, R* GV2, R* GSd, R* b, const R* dctC, const R* Mb,
+__global__ void k_s2_from_sd(const R* __restrict__ Mb, const R* __restrict__ Sd, R* __restrict__ S2, size_t NN,
+                             int L) {
+  const size_t total = NN * L;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i / NN);
+    const size_t pix = i - (size_t)k * NN;
+    R acc = 0;
+    for (int l = 0; l < L; l++) acc = fma(Mb[k * L + l], Sd[(size_t)l * NN + pix], acc);
+    S2[i] = acc;
+  }
+}
+
+template <class R>
+cudaError_t launch_s2_from_sd(const R* Mb, const R* Sd, R* S2, int N, int L, cudaStream_t s) {
+  const size_t total = (size_t)N * N * L;
+  const size_t blocks = (total + 255) / 256;
+  k_s2_from_sd<R><<<(unsigned)(blocks < 152 * 32 ? blocks : 152 * 32), 256, 0, s>>>(Mb, Sd, S2, (size_t)N * N, L);
+  return cudaGetLastError();
+}
+template cudaError_t launch_s2_from_sd<float>(const float*, const float*, float*, int, int, cudaStream_t);
+template cudaError_t launch_s2_from_sd<double>(const double*, const double*, double*, int, int, cudaStream_t);
+
+template <class R>
+cudaError_t launch_spectral_b2(const R* X, R* GP, R* Sd, R* GV, R* GV2, R* GSd, R* S2, R* b, const R* dctC, const R* Mb,
                                int dct_on, int N, int L, IterScalars<R> sc, double* partials, int resid,
                                cudaStream_t s) {
-  if (dct_on) return spectral_b2_dispatch<R, true>(X, GP, Sd, GV, GV2, GSd, b, dctC, Mb, N, L, sc, partials, resid, s);
-  return spectral_b2_dispatch<R, false>(X, GP, Sd, GV, GV2, GSd, b, dctC, Mb, N, L, sc, partials, resid, s);
+  if (dct_on) return spectral_b2_dispatch<R, true>(X, GP, Sd, GV, GV2, GSd, S2, b, dctC, Mb, N, L, sc, partials, resid, s);
+  return spectral_b2_dispatch<R, false>(X, GP, Sd, GV, GV2, GSd, S2, b, dctC, Mb, N, L, sc, partials, resid, s);
 }
-template cudaError_t launch_spectral_b2<float>(const float*, float*, float*, float*, float*, float*, float*,
+template cudaError_t launch_spectral_b2<float>(const float*, float*, float*, float*, float*, float*, float*, float*,
                                                const float*, const float*, int, int, int, IterScalars<float>,
                                                double*, int, cudaStream_t);
-template cudaError_t launch_spectral_b2<double>(const double*, double*, double*, double*, double*, double*, double*,
+template cudaError_t launch_spectral_b2<double>(const double*, double*, double*, double*, double*, double*, double*, double*,
                                                 const double*, const double*, int, int, int, IterScalars<double>,
                                                 double*, int, cudaStream_t);
 

@@ -112,3 +112,26 @@ def test_most_bands(gpu):
     g, o, sc = _views(plan, pb, st, 3)
     errs = _gpu.compare(g, o, sc, keys=tuple(g))
     assert max(errs.values()) < 1e-5, errs
+
+
+@pytest.mark.gpu
+def test_warm_restart_from_a_saved_state(gpu):
+    # the plan keeps S in the Chebyshev basis (M S^) beside S^; a state set from
+    # outside makes it rebuild that array before the next iteration, so that
+    # 3 + (save, restore into a new plan) + 3 iterations equal 6 in one plan
+    c = synth.workload("64x64x8")
+    psf = torch.tensor(c.psf, dtype=torch.float32, device="cuda")
+    y = torch.tensor(c.y, dtype=torch.float32, device="cuda")
+    a = mf.Plan(psf)
+    a.iterate(y, 6, spectral_mask=3, **PRM)
+    b = mf.Plan(psf)
+    b.iterate(y, 3, spectral_mask=3, **PRM)
+    state = b.get_state().clone()
+    cont = mf.Plan(psf)
+    cont.set_state(state)
+    cont.iterate(y, 3, spectral_mask=3, warm_start=1, **PRM)
+    ga, gc = _gpu.gpu_state(a), _gpu.gpu_state(cont)
+    ga["GV2"] = a.get(mf.ARR_GAMMA_V2).double().cpu().numpy()
+    gc["GV2"] = cont.get(mf.ARR_GAMMA_V2).double().cpu().numpy()
+    errs = {k: _gpu.rel_err(gc[k], ga[k]) for k in ga}
+    assert max(errs.values()) < 1e-5, errs
