@@ -72,3 +72,27 @@ def test_create_rejects_bad_sizes_without_touching_the_device():
     assert L.mf_plan_create(64, 4, None, ctypes.byref(h)) == mf.MF_ERR_INVALID
     assert L.mf_plan_create_f64(64, 65, ctypes.c_void_p(16), ctypes.byref(h)) == mf.MF_ERR_INVALID
     L.mf_plan_destroy(None)
+
+
+def test_linear_and_visibility_entry_points_reject_bad_arguments_without_touching_the_device():
+    import ctypes
+
+    h = ctypes.c_void_p()
+    L = mf.lib()
+    fake = ctypes.c_void_p(256)  # never dereferenced: the checks come first
+    # linear convolution plans: N a power of two in [16, 1024]
+    for N in (8, 24, 2048):
+        assert L.mf_plan_create_linear(N, 4, fake, ctypes.byref(h)) == mf.MF_ERR_INVALID
+    assert L.mf_plan_create_linear(64, 4, None, ctypes.byref(h)) == mf.MF_ERR_INVALID
+    # visibility plans: N a power of two in [16, 512], counts >= 0, uv given when any count > 0
+    counts = (ctypes.c_int * 3)(5, 0, 7)
+    for N in (8, 48, 1024):
+        assert L.mf_plan_create_vis(N, 3, counts, fake, None, ctypes.byref(h)) == mf.MF_ERR_INVALID
+    assert L.mf_plan_create_vis(64, 3, None, fake, None, ctypes.byref(h)) == mf.MF_ERR_INVALID
+    bad = (ctypes.c_int * 3)(5, -1, 7)
+    assert L.mf_plan_create_vis(64, 3, bad, fake, None, ctypes.byref(h)) == mf.MF_ERR_INVALID
+    assert L.mf_plan_create_vis(64, 3, counts, None, None, ctypes.byref(h)) == mf.MF_ERR_INVALID
+    assert L.mf_plan_create_vis(64, 1, counts, fake, None, ctypes.byref(h)) == mf.MF_ERR_INVALID  # L >= 2
+    assert L.mf_plan_create_vis(64, 3, counts, fake, None, None) == mf.MF_ERR_INVALID
+    # model visibilities need a visibility plan and an output
+    assert L.mf_vis_predict(None, None, fake, None) == mf.MF_ERR_INVALID
