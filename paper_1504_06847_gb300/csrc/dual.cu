@@ -30,6 +30,22 @@ namespace {
 constexpr int DNT = 256;
 constexpr int DPIX = 32;  // pixels per tile of the spectral part
 
+// four consecutive values from a 16-byte aligned shared-memory address
+__device__ __forceinline__ void ld4(const float* a, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(a);
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* a, double (&v)[4]) {
+  const double2 t0 = reinterpret_cast<const double2*>(a)[0], t1 = reinterpret_cast<const double2*>(a)[1];
+  v[0] = t0.x;
+  v[1] = t0.y;
+  v[2] = t1.x;
+  v[3] = t1.y;
+}
+
 unsigned capped_grid(size_t items) {
   const size_t cap = MF_AUX_GRID;
   return (unsigned)(items < cap ? (items ? items : 1) : cap);
@@ -43,23 +59,34 @@ __global__ void k_dual_snap(const R* __restrict__ b, const R* __restrict__ GP, R
 
 // acc (in pre) = (b - Gamma_P) - pre - sum_k C[k][l] d(Gamma_S W_nu)[k]; ||d(S W_nu)||^2 partials.
 // Tiles of DPIX pixels; thread (g, p): pixel p of the tile, band / frequency rows g, g + 8, ...
-template <class R>
+// acc = (b - Gamma_P) - pre - (dGamma_S W_nu) W_nu^T per pixel spectrum, and
+// ||dS||^2.  A tile is DPIX pixels; warp g of the NG warps owns the bands
+// l = g + j NG (j < ROWS) of every pixel and accumulates them together, reading
+// each dGamma_S value once; the DCT matrix is laid out [k][g][j] in shared
+// memory so that a warp's coefficients of one k are contiguous (vector loads,
+// the same address for every lane).
+template <class R, int ROWS>
 __global__ void __launch_bounds__(DNT) k_dual_spec(const R* __restrict__ b, const R* __restrict__ GP,
                                                     R* __restrict__ pre, const R* __restrict__ Sd,
                                                     const R* __restrict__ Sd0, const R* __restrict__ GSd,
                                                     const R* __restrict__ GSd0, const R* __restrict__ dctC, int NN,
                                                     int L, double* __restrict__ partials) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* C = reinterpret_cast<R*>(smem_raw);  // C[k][l]
-  R* dG = C + L * L;                       // [L][DPIX]
-  const int p = threadIdx.x % DPIX, g = threadIdx.x / DPIX;
   constexpr int NG = DNT / DPIX;
-  for (int e = threadIdx.x; e < L * L; e += DNT) C[e] = dctC[e];
+  static_assert(ROWS % 4 == 0, "vector loads of the coefficients");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* C2 = reinterpret_cast<R*>(smem_raw);  // [L][NG][ROWS]: C[k][g + j NG]
+  R* dG = C2 + (size_t)L * NG * ROWS;      // [L][DPIX]
+  const int p = threadIdx.x % DPIX, g = threadIdx.x / DPIX;
+  for (int e = threadIdx.x; e < L * NG * ROWS; e += DNT) {
+    const int k = e / (NG * ROWS), rem = e % (NG * ROWS);
+    const int l = rem / ROWS + (rem % ROWS) * NG;
+    C2[e] = l < L ? dctC[k * L + l] : (R)0;
+  }
   R ds2 = 0;
   bool bad = false;
   for (int t = blockIdx.x; t < NN / DPIX; t += gridDim.x) {
     const size_t px = (size_t)t * DPIX + p;
-    __syncthreads();  // the previous tile's dG is consumed
+    __syncthreads();  // the previous tile's dG is consumed (and C2 is written)
     for (int k = g; k < L; k += NG) {
       const size_t o = (size_t)k * NN + px;
       dG[k * DPIX + p] = GSd[o] - GSd0[o];
@@ -67,12 +94,29 @@ __global__ void __launch_bounds__(DNT) k_dual_spec(const R* __restrict__ b, cons
       ds2 = fma(d, d, ds2);
     }
     __syncthreads();
-    for (int l = g; l < L; l += NG) {
-      const size_t o = (size_t)l * NN + px;
-      R a = (b[o] - GP[o]) - pre[o];
-      for (int k = 0; k < L; k++) a = fma(-C[k * L + l], dG[k * DPIX + p], a);
-      pre[o] = a;
-      bad |= !isfinite(a);
+    R acc[ROWS];
+#pragma unroll
+    for (int j = 0; j < ROWS; j++) acc[j] = 0;
+    for (int k = 0; k < L; k++) {
+      const R d = dG[k * DPIX + p];
+      const R* c = C2 + ((size_t)k * NG + g) * ROWS;
+#pragma unroll
+      for (int j = 0; j < ROWS; j += 4) {
+        R c4[4];
+        ld4(c + j, c4);
+#pragma unroll
+        for (int i = 0; i < 4; i++) acc[j + i] = fma(c4[i], d, acc[j + i]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < ROWS; j++) {
+      const int l = g + j * NG;
+      if (l < L) {
+        const size_t o = (size_t)l * NN + px;
+        const R a = ((b[o] - GP[o]) - pre[o]) - acc[j];
+        pre[o] = a;
+        bad |= !isfinite(a);
+      }
     }
   }
   R q[Q_COUNT];
@@ -119,12 +163,21 @@ cudaError_t dual_spectral(mf_plan* p, cudaStream_t s) {
   const size_t V = p->cube;
   const int N = p->N, L = p->L, NN = N * N;
   R *pre = base, *Sd0 = base + V, *GSd0 = base + 2 * V;
-  const size_t sm = sizeof(R) * ((size_t)L * L + (size_t)L * DPIX);
-  cudaError_t e = cudaFuncSetAttribute(k_dual_spec<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e) return e;
+  constexpr int NG = DNT / DPIX;
   const unsigned gs = capped_grid((size_t)NN / DPIX);
-  k_dual_spec<R><<<gs, DNT, sm, s>>>((const R*)p->b, (const R*)p->GP, pre, (const R*)p->Sd, Sd0, (const R*)p->GSd,
-                                     GSd0, (const R*)p->dctC, NN, L, p->partials);
+  cudaError_t e;
+  if (L <= 8 * NG) {  // up to 8 bands per warp (L <= 64)
+    const size_t sm = sizeof(R) * ((size_t)L * NG * 8 + (size_t)L * DPIX);
+    if ((e = cudaFuncSetAttribute(k_dual_spec<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
+    k_dual_spec<R, 8><<<gs, DNT, sm, s>>>((const R*)p->b, (const R*)p->GP, pre, (const R*)p->Sd, Sd0,
+                                          (const R*)p->GSd, GSd0, (const R*)p->dctC, NN, L, p->partials);
+  } else {  // L <= 128
+    const size_t sm = sizeof(R) * ((size_t)L * NG * 16 + (size_t)L * DPIX);
+    if ((e = cudaFuncSetAttribute(k_dual_spec<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+      return e;
+    k_dual_spec<R, 16><<<gs, DNT, sm, s>>>((const R*)p->b, (const R*)p->GP, pre, (const R*)p->Sd, Sd0,
+                                           (const R*)p->GSd, GSd0, (const R*)p->dctC, NN, L, p->partials);
+  }
   if ((e = cudaGetLastError())) return e;
   return launch_finalize(p->partials, (int)gs, p->sums, 1, s);
 }
