@@ -171,12 +171,14 @@ cudaError_t dual_spectral(mf_plan* p, cudaStream_t s) {
     if ((e = cudaFuncSetAttribute(k_dual_spec<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
     k_dual_spec<R, 8><<<gs, DNT, sm, s>>>((const R*)p->b, (const R*)p->GP, pre, (const R*)p->Sd, Sd0,
                                           (const R*)p->GSd, GSd0, (const R*)p->dctC, NN, L, p->partials);
-  } else {  // L <= 128
+  } else if constexpr (sizeof(R) == 4) {  // L <= 128 (FP64 plans take at most 64 bands)
     const size_t sm = sizeof(R) * ((size_t)L * NG * 16 + (size_t)L * DPIX);
     if ((e = cudaFuncSetAttribute(k_dual_spec<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
       return e;
     k_dual_spec<R, 16><<<gs, DNT, sm, s>>>((const R*)p->b, (const R*)p->GP, pre, (const R*)p->Sd, Sd0,
                                            (const R*)p->GSd, GSd0, (const R*)p->dctC, NN, L, p->partials);
+  } else {
+    return cudaErrorInvalidValue;
   }
   if ((e = cudaGetLastError())) return e;
   return launch_finalize(p->partials, (int)gs, p->sums, 1, s);

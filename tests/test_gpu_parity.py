@@ -145,6 +145,25 @@ def test_dual_residual_distinct_penalties(dtype, tol):
     assert err < tol, err
 
 
+@pytest.mark.parametrize("L", [100, 128])
+def test_dual_residual_many_bands(L):
+    # more than 64 bands (FP32 only: FP64 plans take at most 64): the spectral
+    # part of the dual residual then gives each thread 16 bands of a pixel
+    # spectrum instead of 8 (100 leaves a ragged last group)
+    dtype, tol = torch.float32, 1e-3
+    prm = dict(mu_eps=0.003, mu_s=0.04, mu_nu=0.015, rho_P=0.7, rho_T=1.3, rho_V=1.9, rho_S=0.6)
+    c = synth.make_cube(32, L, n_sources=3, n_antennas=24, seed=L)
+    pb = oracle.Problem(c.psf, c.y, prm, J=2)
+    _, H = pb.run(3, hist=True)
+    plan = _gpu.run_gpu(c, prm, 3, J=2, dtype=dtype, resid_every=1)
+    rep = plan.report()
+    assert rep["status"] == mf.MF_OK and rep["resid_iter"] == 3
+    errs = {"dual_res": abs(rep["dual_res"] - H[-1, 1]) / H[-1, 1],
+            "primal_res": abs(rep["primal_res"] - H[-1, 0]) / H[-1, 0]}
+    _gpu.log_errors(errs)
+    assert max(errs.values()) < tol, errs
+
+
 def test_deterministic():
     c = synth.workload("64x64x8")
     a = _gpu.gpu_state(_gpu.run_gpu(c, PRM, 7))
