@@ -382,18 +382,30 @@ struct TC {
   static constexpr int OPI = (T * T / WNT) < 8 ? (T * T / WNT) : 8;  // outputs of one synthesis item
   static constexpr int IPT = T * T / (WNT * OPI);                    // synthesis items per thread
   static constexpr int MINB = T == 64 ? 2 : 4;                       // CTAs per SM
+  // the synthesis-only mode (RESID == 2) has no input tile: IN fewer elements
+  // of shared memory, and one more FP32 CTA per SM for the 64 x 64 tiles
+  static constexpr int IN = IR * IP;
+  static constexpr int MINB_SYN = T == 64 ? 3 : 4;
   // the pair planes that follow the input tile start on a 16-byte boundary
   static_assert((IR * IP) % 2 == 0, "input tile size must keep the pair planes aligned");
 };
 
+// CTAs per SM that the level kernels' register budget is set for (FP64 keeps
+// the plain count in the synthesis-only mode: 80 registers would spill)
+template <class R, int T, int RESID>
+constexpr int level_minb() {
+  return RESID == 2 && sizeof(R) == 4 ? TC<T>::MINB_SYN : TC<T>::MINB;
+}
+
 // Shared memory of the T x T level kernels: the input tile, then the pair
 // plane of the row analysis / column synthesis (CR x CP pairs), then the two
 // sub-band pair planes (SR x CP pairs each); level 1 adds its accumulator.
-template <class R, int T>
+// Without an input tile (WITH_IN false) the pair planes start the layout.
+template <class R, int T, bool WITH_IN>
 __device__ __forceinline__ R* tile_smem(R*& ra, R*& sb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* in = reinterpret_cast<R*>(smem_raw);
-  ra = in + TC<T>::IR * TC<T>::IP;
+  ra = in + (WITH_IN ? TC<T>::IN : 0);
   sb = ra + 2 * TC<T>::CR * TC<T>::CP;
   return in;
 }
@@ -726,7 +738,7 @@ __device__ __noinline__ LevelSums<R> level1_basis(const R* in, R* ra, R* sb, R* 
 }
 
 template <class R, int T, int RESID>
-__global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_level1_t(const R* __restrict__ X, R* __restrict__ b,
+__global__ void __launch_bounds__(WNT, level_minb<R, T, RESID>()) k_wav_level1_t(const R* __restrict__ X, R* __restrict__ b,
                                                                   const R* __restrict__ gto, R* __restrict__ gtn,
                                                                   const R* __restrict__ rco, int N, int L,
                                                                   int coarsest, const WavSet<R>* __restrict__ ws,
@@ -734,7 +746,7 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_level1_t(const R* __re
                                                                   double* __restrict__ partials) {
   typedef TC<T> C;
   R *ra, *sb;
-  R* in = tile_smem<R, T>(ra, sb);
+  R* in = tile_smem<R, T, RESID != 2>(ra, sb);
   const int tpd = N / T;
   const int band = blockIdx.y;
   const int y0 = (blockIdx.x / tpd) * T, x0 = (blockIdx.x % tpd) * T;
@@ -821,7 +833,7 @@ __device__ __forceinline__ void prefetch_tile(const R* src, int M, int K, int y0
 // one group unless the grid would be too small to fill the GPU) in one CTA, in
 // turn, with the next basis's tile and coefficients prefetched; writes R_{j-1}.
 template <class R, int T, int RESID>
-__global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_levelj_t(const R* __restrict__ in_img,
+__global__ void __launch_bounds__(WNT, level_minb<R, T, RESID>()) k_wav_levelj_t(const R* __restrict__ in_img,
                                                                   R* __restrict__ out_img,
                                                                   const R* __restrict__ gto, R* __restrict__ gtn,
                                                                   const R* __restrict__ rco, int N, int M, int L,
@@ -829,7 +841,7 @@ __global__ void __launch_bounds__(WNT, TC<T>::MINB) k_wav_levelj_t(const R* __re
                                                                   IterScalars<R> sc,
                                                                   double* __restrict__ partials) {
   R *ra, *sb;
-  R* in = tile_smem<R, T>(ra, sb);
+  R* in = tile_smem<R, T, RESID != 2>(ra, sb);
   const int tpd = M / T;
   const int band = blockIdx.y;
   const int y0 = (blockIdx.x / tpd) * T, x0 = (blockIdx.x % tpd) * T;
@@ -1365,7 +1377,7 @@ static cudaError_t launch_level_t(const R* in, const R* rcoarse, R* out, const R
     dim3 grid(tiles, L);
     const size_t sm1 = sizeof(R) * TC<T>::SMEM1;
     if (resid == 2)
-      return launch_k<R>(k_wav_level1_t<R, T, 2>, grid, sm1, s, in, out, gt_old, gt_new, rcoarse, N, L, coarsest, ws,
+      return launch_k<R>(k_wav_level1_t<R, T, 2>, grid, sm1 - sizeof(R) * TC<T>::IN, s, in, out, gt_old, gt_new, rcoarse, N, L, coarsest, ws,
                          sc, partials);
     if (resid)
       return launch_k<R>(k_wav_level1_t<R, T, 1>, grid, sm1, s, in, out, gt_old, gt_new, rcoarse, N, L, coarsest, ws,
@@ -1376,7 +1388,7 @@ static cudaError_t launch_level_t(const R* in, const R* rcoarse, R* out, const R
   dim3 grid(tiles, L, levelj_groups(tiles, L, nd));
   const size_t sm = sizeof(R) * TC<T>::SMEM;
   if (resid == 2)
-    return launch_k<R>(k_wav_levelj_t<R, T, 2>, grid, sm, s, in, out, gt_old, gt_new, rcoarse, N, M, L, coarsest, ws,
+    return launch_k<R>(k_wav_levelj_t<R, T, 2>, grid, sm - sizeof(R) * TC<T>::IN, s, in, out, gt_old, gt_new, rcoarse, N, M, L, coarsest, ws,
                        sc, partials);
   if (resid)
     return launch_k<R>(k_wav_levelj_t<R, T, 1>, grid, sm, s, in, out, gt_old, gt_new, rcoarse, N, M, L, coarsest, ws,
