@@ -22,6 +22,7 @@ cores instead, one Algorithm-1 iteration of the workload per step.
 Single cases for profiling (no JSON contract line):
   python bench.py --case plain --N 1024 --L 8 --iters 2 [--precision fp32|splitbf16] [--tile 64|32] [--resid]
                    [--spectral-mask 1|2|3]
+  python bench.py --case linear|vis --N 512 --L 32 --iters 2 [--cg-iters 10] [--resid]
   python bench.py --case batch [--batch 16] [--iters 100]
   python bench.py --case backward --N 256 --L 32 --iters 20
   python bench.py --case xstep --N 1024 --L 64
@@ -597,9 +598,28 @@ def run_case(args):
     if args.case == "configs":
         print(json.dumps(measure_configs(stream)))
         return 0
+    prm = synth.WORKLOAD_PARAMS
+    if args.case in ("linear", "vis"):
+        # step I by conjugate gradients, the cubes of the widened-rows measurement
+        with torch.cuda.stream(stream):
+            if args.case == "linear":
+                c = synth.make_cube(args.N, args.L, n_sources=40, n_antennas=128, seed=12)
+                plan = mf.Plan(torch.tensor(c.psf, dtype=torch.float32, device="cuda"), linear=True)
+                y = torch.tensor(c.y, dtype=torch.float32, device="cuda")
+            else:
+                cv = synth.make_visibilities(args.N, args.L, n_sources=40, n_antennas=128, seed=13,
+                                             random_weights=True)
+                plan = mf.Plan.from_visibilities(
+                    args.N, [torch.tensor(q, dtype=torch.float32, device="cuda") for q in cv.uv],
+                    [torch.tensor(w, dtype=torch.float32, device="cuda") for w in cv.weights])
+                y = torch.tensor(np.concatenate(cv.vis).astype(np.complex64), device="cuda")
+            plan.iterate(y, args.iters, cg_iters=args.cg_iters, wavelet_levels=args.J,
+                         resid_every=1 if args.resid else 0, **prm)
+            print(json.dumps(plan.report()))
+            plan.close()
+        return 0
     c = synth.make_cube(args.N, args.L, n_sources=max(2, int(40 * (args.N / 256) ** 2)), n_antennas=128,
                         seed=args.seed)
-    prm = synth.WORKLOAD_PARAMS
     prec = mf.MF_FP32_DCT_SPLITBF16 if args.precision == "splitbf16" else mf.MF_FP32
     with torch.cuda.stream(stream):
         plan = mf.Plan(torch.tensor(c.psf, dtype=torch.float32, device="cuda"))
@@ -630,13 +650,15 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="leave out the batched and differentiable forms")
     ap.add_argument("--precision", default="splitbf16", choices=["splitbf16", "fp32"],
                     help="DCT arithmetic of the spectral step (the cube is FP32 either way)")
-    ap.add_argument("--case", default=None, choices=["plain", "batch", "backward", "xstep", "oracle", "configs"],
+    ap.add_argument("--case", default=None,
+                    choices=["plain", "linear", "vis", "batch", "backward", "xstep", "oracle", "configs"],
                     help="a single run for profiling instead of the benchmark line")
     ap.add_argument("--N", type=int, default=1024)
     ap.add_argument("--L", type=int, default=8)
     ap.add_argument("--J", type=int, default=3)
     ap.add_argument("--iters", type=int, default=2)
     ap.add_argument("--tile", type=int, default=64, choices=[64, 32])
+    ap.add_argument("--cg-iters", type=int, default=10, help="CG iterations of step I (--case linear|vis)")
     ap.add_argument("--resid", action="store_true")
     ap.add_argument("--spectral-mask", type=int, default=1, choices=[1, 2, 3],
                     help="spectral dictionary of --case plain: 1 DCT, 2 Chebyshev, 3 both (FP32 DCT)")
