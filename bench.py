@@ -362,11 +362,12 @@ def measure_forms(stream, xstep_ms=None):
         kw_e1 = dict(synth.PAPER_PARAMS, stream=stream.cuda_stream)
         plan_e1.iterate(y_e1, 3, **kw_e1)
         s.record(stream)
-        plan_e1.iterate(y_e1, 350, **kw_e1)
+        plan_e1.iterate(y_e1, synth.PAPER_ITERS, **kw_e1)
         e.record(stream)
         stream.synchronize()
         t_e1 = s.elapsed_time(e)
-        out["paper_e1_256x256x15"] = {"iters": 350, "ms": t_e1, "voxel_it_per_s": c.y.size * 350 / (t_e1 * 1e-3),
+        out["paper_e1_256x256x15"] = {"iters": synth.PAPER_ITERS, "ms": t_e1,
+                                      "voxel_it_per_s": c.y.size * synth.PAPER_ITERS / (t_e1 * 1e-3),
                                       "params": "Section 4 settings", "dtype": "f32",
                                       "note": "the paper reports about 1.5 h on 15 CPU cores for a 256x256x15 run "
                                               "of 350 iterations"}

@@ -193,9 +193,11 @@ WORKLOADS = {
 WORKLOAD_PARAMS = dict(mu_eps=0.001, mu_s=0.05, mu_nu=0.01,
                        rho_P=1.0, rho_T=1.0, rho_V=1.0, rho_S=1.0)
 
-# The paper's own settings (Section 4).
+# The paper's own settings (Section 4), and its fixed iteration count (it
+# stops after 350 iterations instead of testing the residuals).
 PAPER_PARAMS = dict(mu_eps=0.001, mu_s=0.5, mu_nu=1.0,
                     rho_P=1.0, rho_T=5.0, rho_V=2.0, rho_S=1.0)
+PAPER_ITERS = 350
 
 
 def workload(name: str) -> Cube:

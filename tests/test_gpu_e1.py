@@ -39,7 +39,7 @@ def built():
 def test_two_gaussian_spectral_indices():
     c = synth.two_gaussians()
     prm = synth.PAPER_PARAMS
-    n_iter = 350
+    n_iter = synth.PAPER_ITERS
     plan = mf.Plan(torch.tensor(c.psf, dtype=torch.float32, device="cuda"))
     plan.iterate(torch.tensor(c.y, dtype=torch.float32, device="cuda"), n_iter, **prm)
     x = plan.x()
