@@ -142,6 +142,11 @@ mf_status mf_plan_create_linear(int N, int L, const float* psf_cube, mf_plan** o
  * Both are copied (the caller keeps its buffers).  mf_admm_iterate on this plan
  * takes y_cube = device float [sum n_vis][2], the complex visibilities
  * (re, im), in the same order.  N is a power of two in [16, 512].
+ * The gridding adds the visibilities' contributions with FP32 atomics, so the
+ * last bits of the Toeplitz kernel and of the dirty image (and of the X that
+ * follows) depend on the order the additions land in: results agree to
+ * rounding from run to run, not bit for bit (circular and linear plans are
+ * bitwise reproducible).
  * mf_admm_backward rejects it.  Errors: MF_ERR_INVALID (sizes, NULL, a uv
  * point or weight out of range or not finite), MF_ERR_OOM, MF_ERR_CUDA. */
 mf_status mf_plan_create_vis(int N, int L, const int* n_vis, const float* uv, const float* weights,
@@ -175,9 +180,14 @@ mf_status mf_admm_iterate_f64(mf_plan* p, const double* y_cube, const mf_params*
 /* Batched form: runs n_iter iterations of Algorithm 1 on each of `count`
  * independent FP32 plans (cubes of any N and L; no plan may appear twice),
  * plan i on the dirty cube y_cubes[i] (device pointers), as ONE CUDA graph
- * launch on prm->stream in which every cube is its own branch.  The graph is
- * built and instantiated on each call (host cost) and kept by plans[0] until
- * its next batch call or its destruction.  Per-plan results, state access and
+ * launch on prm->stream in which every cube is its own branch.  A call
+ * identical to the previous batch call with the same plans[0] (same plans in
+ * the same order, y pointers, n_iter, parameters and stream, plan options, and
+ * each plan's Gamma_T buffer, which an odd n_iter swaps) relaunches the graph
+ * captured then; any other call captures and instantiates a new graph (host
+ * cost), which plans[0] keeps until its next batch call or its destruction.
+ * The per-call constants (F(y), the filter, H^T y) are enqueued before the
+ * graph on every call.  Per-plan results, state access and
  * reports are as after mf_admm_iterate.  Per-kernel event timing is suspended
  * inside the graph.  Errors: MF_ERR_INVALID, MF_ERR_CUDA (latched in every plan). */
 mf_status mf_batch_iterate(mf_plan* const* plans, const float* const* y_cubes, int count, const mf_params* prm,
