@@ -53,7 +53,7 @@ typedef enum {
 typedef enum {
   MF_FP32 = 0,                 /* FP32 cube, FP32 DCT */
   MF_FP64 = 1,                 /* FP64 plan (created with mf_plan_create_f64) */
-  MF_FP32_DCT_SPLITBF16 = 2    /* FP32 cube, DCT as split-BF16 tensor-core products */
+  MF_FP32_DCT_SPLITBF16 = 2    /* FP32 cube, DCT as split-BF16 tensor-core products (L <= 64) */
 } mf_precision;
 
 /* Regularisation and penalty parameters (Section 3 and the settings of Section 4). */
@@ -67,8 +67,8 @@ typedef struct {
                                         and on the last one */
   int warm_start;                    /* 0: zero state first (Algorithm 1); 1: continue */
   void* stream;                      /* cudaStream_t; NULL = legacy default stream */
-  int cg_iters;                      /* plans from mf_plan_create_linear: conjugate gradient
-                                        iterations of step I per band (>= 1, default 20) */
+  int cg_iters;                      /* plans from mf_plan_create_linear and _vis: conjugate
+                                        gradient iterations of step I per band (>= 1, default 20) */
   unsigned spectral_mask;            /* spectral dictionary W_nu, a union of orthonormal bases
                                         (step V divides by m_nu rho_V + rho_S): bit 0 the DCT,
                                         bit 1 the Chebyshev basis (mf_spectral_basis); default 1.
@@ -84,8 +84,8 @@ typedef struct {
  *   dual_res   = ||rho_P dP + rho_T W_s^T dT + rho_S dS||^2 + rho_V^2 ||dS W_nu||^2;
  *   objective  = 1/2||Y-HX||^2 + mu_eps/2||X||^2 + mu_s||W_s X||_1 + mu_nu||X W_nu||_1;
  *   x_min      = min(X) (X may carry small negatives; P is its projection).
- * A plan's first call with resid_every > 0 allocates 5 more cubes for the
- * dual residual's snapshots and work arrays (kept until the plan is destroyed). */
+ * A plan's first call with resid_every > 0 allocates 3 more cubes for the
+ * dual residual's snapshots and work array (kept until the plan is destroyed). */
 typedef struct {
   int iters_done;
   int resid_iter;      /* iteration index the residual fields refer to (-1: none) */
@@ -106,7 +106,7 @@ void mf_params_default(mf_params* p);
  * success *out owns all device memory of the plan (see mf_plan_device_bytes).
  * Errors: MF_ERR_INVALID (sizes, NULL), MF_ERR_OOM, MF_ERR_CUDA. */
 mf_status mf_plan_create(int N, int L, const float* psf_cube, mf_plan** out);
-/* Same with an FP64 plan (all cubes double). */
+/* Same with an FP64 plan (all cubes double); L <= 64. */
 mf_status mf_plan_create_f64(int N, int L, const double* psf_cube, mf_plan** out);
 
 /* An FP32 plan whose H_l is the LINEAR ("same"-size) convolution by each
@@ -257,7 +257,7 @@ typedef enum {
   MF_K_SETUP = 7,      /* per-call constants: F(y), g, c; zeroing of the state */
   MF_K_REDUCE = 8,     /* FP64 fold of the residual partials */
   MF_K_DUAL = 9,       /* dual residual: snapshot before step I, reduction after the iteration */
-  MF_K_CG = 10,        /* step I of a linear-convolution plan: conjugate gradients, 2N FFTs */
+  MF_K_CG = 10,        /* step I of a linear or visibility plan: conjugate gradients, 2N FFTs */
   MF_K_COUNT = 11
 } mf_kernel;
 
