@@ -40,11 +40,16 @@ def build(force: bool = False) -> str:
 
 
 def lib():
+    """The oracle library; MF_ORACLE_LIB names another build of mf_oracle.c to
+    load instead (the planted-mistake tests run the pins against mutants)."""
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = ctypes.CDLL(_LIB)
+            path = os.environ.get("MF_ORACLE_LIB")
+            if not path:
+                build()
+                path = _LIB
+            L = ctypes.CDLL(path)
             dp = ctypes.POINTER(ctypes.c_double)
             ip = ctypes.POINTER(ctypes.c_int)
             c_int = ctypes.c_int
