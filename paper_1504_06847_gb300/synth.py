@@ -200,6 +200,15 @@ PAPER_PARAMS = dict(mu_eps=0.001, mu_s=0.5, mu_nu=1.0,
 PAPER_ITERS = 350
 
 
+def asymmetric_psf(psf: np.ndarray, seed: int, depth: float = 0.3) -> np.ndarray:
+    """The PSF cube multiplied pixel by pixel by 1 + depth U(-1, 1): the same
+    scale, no point symmetry about (N/2, N/2).  The recipe's PSFs are
+    point-symmetric (every uv cell comes with its mirror), for which H^T = H;
+    this variant makes the transposed operator differ from H."""
+    rng = np.random.default_rng(seed)
+    return psf * (1.0 + depth * rng.uniform(-1.0, 1.0, size=psf.shape))
+
+
 def workload(name: str) -> Cube:
     return make_cube(**WORKLOADS[name])
 

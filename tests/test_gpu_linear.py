@@ -9,6 +9,8 @@ count, so FP32 rounding moves it by a small multiple of FP32 epsilon times the
 condition of the few Krylov steps taken.
 """
 
+import types
+
 import numpy as np
 import pytest
 
@@ -51,6 +53,18 @@ def test_linear_plan_matches_oracle(N, L, n_iter, cg_iters):
     errs = _gpu.compare(_gpu.gpu_state(plan), _gpu.oracle_view(pb, st), _gpu.scales(pb, st))
     assert max(errs.values()) < 1e-5, errs
     assert abs(rep["objective"] - H[-1, 3]) < 1e-5 * H[-1, 3]
+
+
+def test_asymmetric_psf():
+    # H^T is applied with the conjugate transfer function (the mode-5 column
+    # pass); with the recipe's point-symmetric PSFs H^T = H would hide a mistake
+    c = synth.make_cube(64, 4, n_sources=4, n_antennas=32, seed=87)
+    psf = synth.asymmetric_psf(c.psf, seed=87)
+    pb = oracle.Problem(psf, c.y, PRM, conv="linear", cg_iters=10)
+    st, _ = pb.run(3)
+    plan = _run(types.SimpleNamespace(psf=psf, y=c.y), 3, 10)
+    errs = _gpu.compare(_gpu.gpu_state(plan), _gpu.oracle_view(pb, st), _gpu.scales(pb, st))
+    assert max(errs.values()) < 1e-5, errs
 
 
 def test_first_step_is_the_cg_solve_of_hty():

@@ -9,6 +9,8 @@ Sizes span several tiles of every kernel and the ragged cases (N = 16 with a
 2 x 2 coarsest band, L not a power of two, masks without Db1, J = 1).
 """
 
+import types
+
 import numpy as np
 import pytest
 
@@ -161,6 +163,19 @@ def test_dual_residual_many_bands(L):
     errs = {"dual_res": abs(rep["dual_res"] - H[-1, 1]) / H[-1, 1],
             "primal_res": abs(rep["primal_res"] - H[-1, 0]) / H[-1, 0]}
     _gpu.log_errors(errs)
+    assert max(errs.values()) < tol, errs
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float32, 1e-5), (torch.float64, 1e-10)])
+def test_asymmetric_psf(dtype, tol):
+    # the recipe's PSFs are point-symmetric (H^T = H); this one is not, so the
+    # conjugate filter of step I and H^T y are exercised
+    c = synth.make_cube(32, 4, n_sources=4, n_antennas=32, seed=55)
+    psf = synth.asymmetric_psf(c.psf, seed=55)
+    pb = oracle.Problem(psf, c.y, PRM)
+    st, _ = pb.run(10)
+    plan = _gpu.run_gpu(types.SimpleNamespace(psf=psf, y=c.y), PRM, 10, dtype=dtype)
+    errs = _gpu.compare(_gpu.gpu_state(plan), _gpu.oracle_view(pb, st), _gpu.scales(pb, st))
     assert max(errs.values()) < tol, errs
 
 

@@ -22,6 +22,26 @@ CASES = [
      "return pb->mu_eps + pb->rho_S + pb->rho_P + pb->nb * pb->rho_T;",
      "return pb->mu_eps + pb->rho_S + pb->rho_P + pb->rho_T;",
      "test_oracle_steps.py", "step_I"),
+    ("hty_without_conjugate", "set-up: H y formed in place of H^T y (the conjugate filter dropped)",
+     "ti[i] = hre[i] * yim[i] - him[i] * yre[i];",
+     "ti[i] = hre[i] * yim[i] + him[i] * yre[i];",
+     "test_oracle_steps.py", "asymmetric"),
+    ("make_b_without_gamma_S", "Eq. matB: the Gamma_S term of b dropped",
+     "bl[i] = HtY[q] + GP[q] + pb->rho_P * P[q] + GS[q] + pb->rho_S * S[q];",
+     "bl[i] = HtY[q] + GP[q] + pb->rho_P * P[q] + pb->rho_S * S[q];",
+     "test_oracle_steps.py", "step_I"),
+    ("fft_direction", "the 2-D FFT run in the inverse direction",
+     "fft2_image(re + (long)i * N * N, im + (long)i * N * N, N, sign > 0, twr, twi, lr, li);",
+     "fft2_image(re + (long)i * N * N, im + (long)i * N * N, N, sign < 0, twr, twi, lr, li);",
+     "test_oracle_transforms.py", "fft"),
+    ("dct_index_swap", "DCT-II matrix with the frequency and sample indices swapped (its transpose)",
+     "C[k * L + l] = a * cos(M_PI * (2.0 * l + 1.0) * k / (2.0 * L));",
+     "C[k * L + l] = a * cos(M_PI * (2.0 * k + 1.0) * l / (2.0 * L));",
+     "test_oracle_transforms.py", "dct"),
+    ("primal_residual_without_T", "primal residual: the ||T - W_s X||^2 term dropped",
+     "double r2 = sumsq_diff(P, X, V_) + sumsq_diff(T, Z, VT) + sumsq_diff(S, X, V_);",
+     "double r2 = sumsq_diff(P, X, V_) + sumsq_diff(S, X, V_);",
+     "test_oracle_reductions.py", "history_matches"),
     ("dwt_index_shift", "DWT analysis reads x[(2i + n + 1) mod M] instead of x[(2i + n) mod M]",
      "double v = x[(2 * i + n) % M];",
      "double v = x[(2 * i + n + 1) % M];",

@@ -72,25 +72,53 @@ def test_binary_mask_psf_gives_two_valued_filter():
         assert np.max(np.abs(pb.him[l])) < 1e-12
 
 
-@pytest.mark.parametrize("mask", [0x1FF, 0x0A2])
-def test_step_I_is_the_X_minimiser(mask):
-    c, pb = _problem(mask=mask)
-    st = _random_state(pb)
-    X = pb.solve(pb.make_b(st))
+def _step_I_minimiser(pb, psf, y, st):
+    """Per band, the X minimising the augmented Lagrangian with the other
+    variables fixed, as stacked dense least squares."""
     p = pb.params
-    N, L = pb.N, pb.L
+    N = pb.N
     Ws = [_dense.dwt_matrix(h, N, pb.J) for _, h in pb.bases]
     I = np.eye(N * N)
-    for l in range(L):
-        H = _dense.conv_matrix(c.psf[l])
+    out = []
+    for l in range(pb.L):
+        H = _dense.conv_matrix(psf[l])
         rows = [H, np.sqrt(p["mu_eps"]) * I, np.sqrt(p["rho_P"]) * I, np.sqrt(p["rho_S"]) * I]
-        rhs = [c.y[l].ravel(), np.zeros(N * N),
+        rhs = [y[l].ravel(), np.zeros(N * N),
                np.sqrt(p["rho_P"]) * (st["P"][l] + st["GP"][l] / p["rho_P"]).ravel(),
                np.sqrt(p["rho_S"]) * (st["S"][l] + st["GS"][l] / p["rho_S"]).ravel()]
         for k, W in enumerate(Ws):
             rows.append(np.sqrt(p["rho_T"]) * W)
             rhs.append(np.sqrt(p["rho_T"]) * (st["T"][k, l] + st["GT"][k, l] / p["rho_T"]).ravel())
-        x_ref = np.linalg.lstsq(np.vstack(rows), np.concatenate(rhs), rcond=None)[0]
+        out.append(np.linalg.lstsq(np.vstack(rows), np.concatenate(rhs), rcond=None)[0])
+    return out
+
+
+@pytest.mark.parametrize("mask", [0x1FF, 0x0A2])
+def test_step_I_is_the_X_minimiser(mask):
+    c, pb = _problem(mask=mask)
+    st = _random_state(pb)
+    X = pb.solve(pb.make_b(st))
+    for l, x_ref in enumerate(_step_I_minimiser(pb, c.psf, c.y, st)):
+        assert np.max(np.abs(X[l].ravel() - x_ref)) < 1e-11 * max(1.0, np.abs(x_ref).max())
+
+
+def test_asymmetric_psf_setup_and_step_I():
+    # The recipe's PSFs are point-symmetric about (N/2, N/2), so for them
+    # H^T = H and a missing conjugate in H^T y or in the filter goes unseen;
+    # this PSF has no symmetry.
+    rng = np.random.default_rng(5)
+    N, L = 8, 3
+    psf = rng.uniform(-0.3, 0.3, size=(L, N, N))
+    psf[:, N // 2, N // 2] = 1.0
+    y = rng.normal(size=(L, N, N))
+    pb = oracle.Problem(psf, y, PRM, J=2)
+    for l in range(L):
+        H = _dense.conv_matrix(psf[l])
+        assert np.abs(H - H.T).max() > 0.1
+        assert np.max(np.abs(pb.HtY[l].ravel() - H.T @ y[l].ravel())) < 1e-12
+    st = _random_state(pb)
+    X = pb.solve(pb.make_b(st))
+    for l, x_ref in enumerate(_step_I_minimiser(pb, psf, y, st)):
         assert np.max(np.abs(X[l].ravel() - x_ref)) < 1e-11 * max(1.0, np.abs(x_ref).max())
 
 
