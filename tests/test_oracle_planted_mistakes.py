@@ -82,6 +82,10 @@ CASES = [
      "int r = ((u - N / 2) % M + M) % M, c = ((v - N / 2) % M + M) % M;",
      "int r = ((u - N / 2 + 1) % M + M) % M, c = ((v - N / 2) % M + M) % M;",
      "test_oracle_linear.py", "dense_linear_convolution or delta_psf"),
+    ("linear_adjoint_without_conjugate", "linear H: H^T applied with the transfer function itself",
+     "double hr = h2re[i], hi = adjoint ? -h2im[i] : h2im[i];",
+     "double hr = h2re[i], hi = h2im[i];",
+     "test_oracle_linear.py", "dense_linear_convolution"),
     ("visibility_phase_sign", "visibility operator: exp(+2 pi i ...) instead of exp(-2 pi i ...)",
      "double a = -2.0 * M_PI * f * (double)(n - N / 2) / (double)N;",
      "double a = 2.0 * M_PI * f * (double)(n - N / 2) / (double)N;",
